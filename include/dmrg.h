@@ -1,0 +1,215 @@
+/*
+ * dmrg.h -- C-ABI of libdmrg.so: the two-site ab initio DMRG hot path
+ * (arXiv:2311.02854) on one GB300 (sm_103a).
+ *
+ * The library computes the Davidson sigma product sigma = H psi of Eq. (Sigma)
+ * for the two-site wavefunction of Sec. 2.1, with the renormalised normal and
+ * complementary operators of Eq. (qops) kept in device memory, the
+ * renormalisation update of Eq. (Renorm), the Davidson eigensolver and the
+ * decimation step (Sec. 2.1, 2.3).  Every arithmetic step runs in the
+ * library's own CUDA kernels; the host only plans (index tables, integral
+ * coefficient tables, the choice of kept states from eigenvalues).
+ *
+ * Conventions
+ *  - Spin orbital p = 2*i + s (s = 0 alpha, 1 beta) of spatial orbital i;
+ *    Jordan-Wigner order (1a, 1b, 2a, 2b, ...).
+ *  - Local basis of a site (Sec. 2.1, after Eq. MPS): n = 0 vac, 1 beta,
+ *    2 alpha, 3 alpha-beta, with |ab> = a+_a a+_b |vac>.
+ *  - Hamiltonian Eq. (Hsq) with h (K x K) and chemist integrals
+ *    (pq|rs) = sum_X chol[X][p][q] chol[X][r][s].
+ *  - Two-site wavefunction layout ("canonical layout"): sectors ordered by
+ *    (left sector il, c1 = 0..3, c2 = 0..3), the right sector being the one
+ *    whose bond label is label(il) + q(c1) + q(c2); each sector block is
+ *    d_l x d_r, row-major, blocks packed back to back (see dmrg_layout).
+ *  - Bond b lies between sites b and b+1 (sites numbered 1..K); bond labels
+ *    are the (N, 2Sz) quantum numbers of sites 1..b.
+ *
+ * Ownership: psi / sigma / diag buffers are owned by the caller.  A plan owns
+ * every device allocation it makes (operator store, intermediates, work
+ * lists, scratch) and frees it in dmrg_destroy.
+ *
+ * Errors: every call returns a dmrg_status; nothing aborts.  A device-side
+ * failure (a kernel wait that gave up, a NaN seen by a check) is reported
+ * through a device error word read after the stream synchronises.
+ * dmrg_last_error() gives a one-line description of the last failure.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls are synchronous with respect to the host unless stated.
+ */
+#ifndef DMRG_H
+#define DMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmrg_plan_s* dmrg_plan_t;
+
+typedef enum {
+    DMRG_OK = 0,
+    DMRG_EINVAL = -1,     /* bad argument (sizes, quantum numbers, file) */
+    DMRG_ENOMEM = -2,     /* device allocation would exceed the budget / failed */
+    DMRG_ECUDA = -3,      /* a CUDA runtime call failed */
+    DMRG_ENUMERIC = -4,   /* NaN/Inf or breakdown detected */
+    DMRG_ETIMEOUT = -5,   /* a bounded device wait gave up */
+    DMRG_ENOTCONV = -6,   /* Davidson did not reach the tolerance */
+    DMRG_EIO = -7         /* file could not be read or written */
+} dmrg_status;
+
+/* Arithmetic of the operator store and of the sigma / renormalisation GEMMs.
+ * FP64: everything in double precision (reference GPU path).
+ * BF16X3: operators, wavefunction and intermediates split x = hi + lo into two
+ *   bf16 numbers; each product uses hi*hi + hi*lo + lo*hi on the tcgen05
+ *   tensor cores with FP32 accumulation in tensor memory; sigma is summed
+ *   into FP64.  Davidson, orthogonalisation, Ritz, residuals, energies and
+ *   decimation stay FP64.
+ * BF16: as BF16X3 with only the hi part (one product per tile). */
+typedef enum { DMRG_FP64 = 0, DMRG_BF16X3 = 1, DMRG_BF16 = 2 } dmrg_precision;
+
+typedef enum { DMRG_PRECOND_JACOBI = 0, DMRG_PRECOND_MLP = 1 } dmrg_precond;
+
+typedef struct {
+    int precision;          /* dmrg_precision */
+    int n_roots;            /* roots kept by Davidson (state-averaged decimation if > 1) */
+    double tol;             /* Davidson residual 2-norm tolerance */
+    int max_iter;           /* Davidson iterations per bond */
+    int max_space;          /* Davidson subspace size (0 => 20 * n_roots) */
+    int precond;            /* dmrg_precond */
+    int fp64_final;         /* 1: mixed modes end each Davidson with one FP64 sigma
+                               and an FP64 Rayleigh quotient */
+    int64_t mem_budget;     /* device bytes the plan may hold (0 => 90% of free) */
+    int64_t scratch_bytes;  /* sigma GEMM scratch per chunk (0 => automatic) */
+    int keep_envs;          /* 1: keep every bond's environment (sweeps) */
+    int verbose;            /* 0 silent, 1 per-bond lines on stderr */
+} dmrg_options;
+
+typedef struct {
+    int64_t sigma_calls;          /* dmrg_sigma invocations (all vectors) */
+    double sigma_flops;           /* algorithmic FLOPs of one sigma (current bond, one vector) */
+    double sigma_ms_last;         /* device time of the last sigma call */
+    double interm_flops;          /* FLOPs of forming the bond's intermediates */
+    double renorm_flops_last;     /* FLOPs of the last renormalisation */
+    double ms_interm, ms_gemm, ms_renorm, ms_davidson, ms_decim, ms_hdiag;
+    int64_t n_terms;              /* sigma terms at the current bond */
+    int64_t n_items;              /* (term x sector) GEMM items at the current bond */
+    int64_t store_bytes;          /* operator store bytes of the current L and R */
+    int64_t interm_bytes;         /* intermediate bytes at the current bond */
+    int64_t device_bytes;         /* everything the plan holds on the device */
+    int64_t kernel_launches;      /* kernels launched by the library since the plan was made */
+    int64_t precond_fallbacks;    /* MLP -> Jacobi fallbacks */
+    int davidson_iters_last;
+} dmrg_stats_t;
+
+/* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */
+void dmrg_default_options(dmrg_options* opt);
+
+/* Create a plan (Sec. 2.3: qops of a bond, Eq. Hsq integrals).
+ *  h        K*K row-major one-electron integrals (host), copied.
+ *  chol     n_chol*K*K Cholesky vectors L[X][p][q] (host), copied; the
+ *           two-electron integrals are (pq|rs) = sum_X L[X][p][q] L[X][r][s],
+ *           formed on the device.
+ *  e_core   constant energy added to reported energies.
+ *  K,N,twoS orbitals, electrons, 2*Sz; N <= 2K, |twoS| <= min(N, 2K-N),
+ *           N + twoS even.
+ *  D        bond dimension used by dmrg_sweep when D_schedule is NULL.
+ *  mps_path binary MPS file (format of synthetic_inputs.write_mps): sectors
+ *           of every bond and block-sparse site tensors, left-orthonormal
+ *           left of the centre, right-orthonormal right of centre+1.
+ * Returns DMRG_EINVAL on inconsistent sizes or file, DMRG_EIO if unreadable. */
+dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_core,
+                      int K, int N, int twoS, int D, const dmrg_options* opt,
+                      const char* mps_path, dmrg_plan_t* out);
+
+/* Make bond (k, k+1) current (1 <= k <= K-1): renormalise (Eq. Renorm) the
+ * left block of sites 1..k-1 and the right block of sites k+2..K from the
+ * MPS, form the bond's intermediates (integral-weighted operator sums,
+ * Sec. 2.2 "intermediates") and the sigma work list.  The MPS must be
+ * left-orthonormal on 1..k-1 and right-orthonormal on k+2..K. */
+dmrg_status dmrg_set_bond(dmrg_plan_t plan, int k, void* stream);
+
+/* Canonical layout of the current bond.  dim = total length; n_sectors =
+ * number of sector blocks.  If offsets != NULL it receives n_sectors+1
+ * offsets; if qn != NULL it receives 6 ints per sector:
+ * (N_L, 2Sz_L, c1, c2, d_l, d_r). */
+dmrg_status dmrg_layout(dmrg_plan_t plan, int64_t* dim, int* n_sectors, int64_t* offsets, int* qn);
+
+/* sigma = H psi (Eq. Sigma) for nvec vectors stored back to back (device,
+ * FP64, canonical layout, length nvec*dim each).  psi and sigma must not
+ * overlap.  Intermediate products go through the plan's scratch. */
+dmrg_status dmrg_sigma(dmrg_plan_t plan, const double* psi_dev, double* sigma_dev, int nvec,
+                       void* stream);
+
+/* Same as dmrg_sigma with HOST buffers (copies to and from the device inside;
+ * the end-to-end path of the benchmark). */
+dmrg_status dmrg_sigma_host(dmrg_plan_t plan, const double* psi_host, double* sigma_host,
+                            int nvec, void* stream);
+
+/* Diagonal of H_eff at the current bond (device, FP64, canonical layout). */
+dmrg_status dmrg_hdiag(dmrg_plan_t plan, double* diag_dev, void* stream);
+
+/* Davidson (Sec. 2.1) for the lowest n_roots eigenpairs at the current bond.
+ *  psi_dev  in: n_roots guesses, out: Ritz vectors (device, FP64).
+ *  energies out (host): n_roots eigenvalues + e_core.
+ *  iters    out (host): iterations used (may be NULL).
+ *  precond  dmrg_precond; MLP falls back to Jacobi (counted in stats) if its
+ *           correction is not finite or not a descent direction.
+ * Returns DMRG_ENOTCONV if max_iter is reached above tol (energies filled). */
+dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi_dev, int n_roots, double tol, int max_iter,
+                          int precond, double* energies, int* iters, void* stream);
+
+/* Decimation (Sec. 2.1): truncate the current bond's two-site vectors psi_dev
+ * (n_roots of them; state-averaged density matrix if > 1) to at most D states,
+ * update A[k] (forward) or A[k+1] (backward), renormalise the grown block and
+ * move to the next bond.  next_psi_dev (may be NULL) receives the guess for the
+ * next bond (its length is dmrg_layout of the new bond times n_roots; query the
+ * size with next_dim). */
+dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi_dev, int n_roots, int D, int forward,
+                          double* discarded, double* next_psi_dev, int64_t* next_dim, void* stream);
+
+/* Two-dot sweeps from bond (1,2): forward over bonds 1..K-2 then backward over
+ * K-1..2 (Sec. 2.3).  energies[s], discarded[s]: lowest energy at the last bond
+ * and largest discarded weight of sweep s.  D_schedule (may be NULL) gives the
+ * bond dimension of each sweep. */
+dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, double* energies,
+                       double* discarded, void* stream);
+
+/* Write the current MPS (same format as the input file). */
+dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path);
+
+dmrg_status dmrg_stats(dmrg_plan_t plan, dmrg_stats_t* out);
+
+/* One-line description of the last error of this plan (or of plan creation
+ * if plan is NULL).  The string is owned by the library. */
+const char* dmrg_last_error(dmrg_plan_t plan);
+
+void dmrg_destroy(dmrg_plan_t plan);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry point used by the unit tests (the same grouped GEMM
+ * engine that runs every sigma, renormalisation and intermediate product).
+ * Computes, for each of n_out output blocks o (host arrays of n_out):
+ *   C_o (m_o x n_o, row-major at c + c_off[o], ld n_o)
+ *       = sum over segments s in [seg_beg[o], seg_beg[o+1]) of
+ *         alpha[s] * op(A_s) * op(B_s)
+ * where A_s is m_o x k[s] at a + a_off[s] (row-major ld lda[s], or its
+ * transpose if a_tr[s]) and B_s is k[s] x n_o at b + b_off[s] (ld ldb[s], or
+ * transposed if b_tr[s]).  a, b, c are device FP64 buffers.  precision
+ * selects the FP64 engine or the bf16 tensor-core engine (operands are split
+ * into bf16 hi/lo on the device for BF16X3).
+ * ------------------------------------------------------------------------ */
+dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int* n,
+                              const int64_t* c_off, const int* seg_beg, const int* k,
+                              const int64_t* a_off, const int* lda, const int* a_tr,
+                              const int64_t* b_off, const int* ldb, const int* b_tr,
+                              const double* alpha, const double* a, const double* b, double* c,
+                              void* stream);
+
+/* Library build / device information: writes a short string. */
+const char* dmrg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_H */

@@ -1,0 +1,10 @@
+"""Python binding of libdmrg (two-site ab initio DMRG hot path on GB300).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels behind the C-ABI declared in ``include/dmrg.h``.  Device buffers are
+passed as raw pointers (``torch.Tensor.data_ptr()`` or an int); the library
+never sees torch types.  Importing does not require a GPU; creating a plan
+does, and fails loudly if ``libdmrg.so`` has not been built.
+"""
+from ._lib import (DMRG_BF16, DMRG_BF16X3, DMRG_FP64, DMRG_PRECOND_JACOBI, DMRG_PRECOND_MLP,  # noqa: F401
+                   DMRGError, Options, Plan, Stats, grouped_gemm, lib, lib_path, version)

@@ -1,0 +1,253 @@
+"""ctypes binding of libdmrg.so: same names as the C-ABI, argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+DMRG_FP64, DMRG_BF16X3, DMRG_BF16 = 0, 1, 2
+DMRG_PRECOND_JACOBI, DMRG_PRECOND_MLP = 0, 1
+STATUS = {0: "DMRG_OK", -1: "DMRG_EINVAL", -2: "DMRG_ENOMEM", -3: "DMRG_ECUDA", -4: "DMRG_ENUMERIC",
+          -5: "DMRG_ETIMEOUT", -6: "DMRG_ENOTCONV", -7: "DMRG_EIO"}
+
+
+class DMRGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("n_roots", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("max_space", C.c_int), ("precond", C.c_int), ("fp64_final", C.c_int),
+                ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
+                ("verbose", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sigma_calls", C.c_int64), ("sigma_flops", C.c_double), ("sigma_ms_last", C.c_double),
+                ("interm_flops", C.c_double), ("renorm_flops_last", C.c_double),
+                ("ms_interm", C.c_double), ("ms_gemm", C.c_double), ("ms_renorm", C.c_double),
+                ("ms_davidson", C.c_double), ("ms_decim", C.c_double), ("ms_hdiag", C.c_double),
+                ("n_terms", C.c_int64), ("n_items", C.c_int64), ("store_bytes", C.c_int64),
+                ("interm_bytes", C.c_int64), ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("precond_fallbacks", C.c_int64), ("davidson_iters_last", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib_path():
+    return os.path.join(HERE, "libdmrg.so")
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_L = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "dmrg_default_options": (None, [C.POINTER(Options)]),
+    "dmrg_version": (C.c_char_p, []),
+    "dmrg_plan": (C.c_int, [_D, _D, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                            C.POINTER(Options), C.c_char_p, C.POINTER(_P)]),
+    "dmrg_set_bond": (C.c_int, [_P, C.c_int, _P]),
+    "dmrg_layout": (C.c_int, [_P, _L, _I, _L, _I]),
+    "dmrg_sigma": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dmrg_sigma_host": (C.c_int, [_P, _D, _D, C.c_int, _P]),
+    "dmrg_hdiag": (C.c_int, [_P, _P, _P]),
+    "dmrg_davidson": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _D, _I, _P]),
+    "dmrg_decimate": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _D, _P, _L, _P]),
+    "dmrg_sweep": (C.c_int, [_P, C.c_int, _I, _D, _D, _P]),
+    "dmrg_save_mps": (C.c_int, [_P, C.c_char_p]),
+    "dmrg_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "dmrg_last_error": (C.c_char_p, [_P]),
+    "dmrg_destroy": (None, [_P]),
+    "dmrg_grouped_gemm": (C.c_int, [C.c_int, C.c_int, _I, _I, _L, _I, _I, _L, _I, _I, _L, _I, _I, _D,
+                                    _P, _P, _P, _P]),
+}
+
+
+def lib():
+    """Load libdmrg.so from the package directory (raises if it is missing)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdmrg.so not built ({path}); run python -m paper_2311_02854_gb300.build")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def version():
+    return lib().dmrg_version().decode()
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor, numpy array or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _check(code, plan_handle=None):
+    if code != 0:
+        msg = lib().dmrg_last_error(plan_handle).decode()
+        raise DMRGError(code, msg)
+
+
+def default_options(**kw):
+    o = Options()
+    lib().dmrg_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """dmrg_plan: integrals + MPS file -> plan.  ``close()`` calls dmrg_destroy."""
+
+    def __init__(self, h, chol, K, N, twoS, D, mps_path, e_core=0.0, options=None, **kw):
+        L = lib()
+        self._h = np.ascontiguousarray(h, dtype=np.float64)
+        self._chol = np.ascontiguousarray(chol, dtype=np.float64)
+        opts = options if options is not None else default_options(**kw)
+        self.options = opts
+        handle = _P()
+        code = L.dmrg_plan(_dptr(self._h), _dptr(self._chol), int(self._chol.shape[0]), float(e_core),
+                           int(K), int(N), int(twoS), int(D), C.byref(opts), str(mps_path).encode(),
+                           C.byref(handle))
+        _check(code, None)
+        self.handle = handle
+        self.K, self.N, self.twoS = K, N, twoS
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dmrg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        code = getattr(lib(), name)(self.handle, *args)
+        _check(code, self.handle)
+        return code
+
+    def set_bond(self, k, stream=None):
+        self._call("dmrg_set_bond", int(k), _stream(stream))
+
+    def layout(self):
+        dim = C.c_int64()
+        ns = C.c_int()
+        self._call("dmrg_layout", C.byref(dim), C.byref(ns), None, None)
+        offs = np.zeros(ns.value + 1, dtype=np.int64)
+        qn = np.zeros(6 * ns.value, dtype=np.int32)
+        self._call("dmrg_layout", C.byref(dim), C.byref(ns), offs.ctypes.data_as(_L),
+                   qn.ctypes.data_as(_I))
+        return dim.value, offs, qn.reshape(-1, 6)
+
+    @property
+    def dim(self):
+        return self.layout()[0]
+
+    def sigma(self, psi, out, nvec=1, stream=None):
+        self._call("dmrg_sigma", _ptr(psi), _ptr(out), int(nvec), _stream(stream))
+
+    def sigma_host(self, psi, out, nvec=1, stream=None):
+        assert psi.dtype == np.float64 and out.dtype == np.float64
+        self._call("dmrg_sigma_host", _dptr(psi), _dptr(out), int(nvec), _stream(stream))
+
+    def hdiag(self, out, stream=None):
+        self._call("dmrg_hdiag", _ptr(out), _stream(stream))
+
+    def davidson(self, psi, n_roots=1, tol=1e-6, max_iter=200, precond=DMRG_PRECOND_JACOBI, stream=None):
+        e = np.zeros(n_roots)
+        it = C.c_int()
+        code = getattr(lib(), "dmrg_davidson")(self.handle, _ptr(psi), int(n_roots), float(tol), int(max_iter),
+                                                int(precond), _dptr(e), C.byref(it), _stream(stream))
+        if code not in (0, -6):
+            _check(code, self.handle)
+        return e, it.value, code == 0
+
+    def decimate(self, psi, n_roots, D, forward, next_psi=None, next_cap=0, stream=None):
+        w = np.zeros(1)
+        nd = C.c_int64(int(next_cap))
+        self._call("dmrg_decimate", _ptr(psi), int(n_roots), int(D), int(bool(forward)), _dptr(w),
+                   _ptr(next_psi), C.byref(nd), _stream(stream))
+        return float(w[0]), nd.value
+
+    def sweep(self, n_sweeps, D_schedule=None, stream=None):
+        e = np.zeros(n_sweeps)
+        w = np.zeros(n_sweeps)
+        ds = None
+        if D_schedule is not None:
+            arr = np.ascontiguousarray(D_schedule, dtype=np.int32)
+            ds = arr.ctypes.data_as(_I)
+        code = getattr(lib(), "dmrg_sweep")(self.handle, int(n_sweeps), ds, _dptr(e), _dptr(w), _stream(stream))
+        if code not in (0, -6):
+            _check(code, self.handle)
+        return e, w
+
+    def save_mps(self, path):
+        self._call("dmrg_save_mps", str(path).encode())
+
+    def stats(self):
+        s = Stats()
+        self._call("dmrg_stats", C.byref(s))
+        return s.as_dict()
+
+
+def grouped_gemm(precision, blocks, a, b, c, stream=None):
+    """dmrg_grouped_gemm.  ``blocks``: list of (m, n, c_off, [segments]) with
+    segment = (k, a_off, lda, a_tr, b_off, ldb, b_tr, alpha); a, b, c device FP64."""
+    ms, ns, coff, beg = [], [], [], [0]
+    k, ao, la, at, bo, lb, bt, al = [], [], [], [], [], [], [], []
+    for (m, n, co, segs) in blocks:
+        ms.append(m)
+        ns.append(n)
+        coff.append(co)
+        for s in segs:
+            k.append(s[0]); ao.append(s[1]); la.append(s[2]); at.append(s[3])
+            bo.append(s[4]); lb.append(s[5]); bt.append(s[6]); al.append(s[7])
+        beg.append(len(k))
+    i32 = lambda v: np.ascontiguousarray(v, dtype=np.int32)  # noqa: E731
+    i64 = lambda v: np.ascontiguousarray(v, dtype=np.int64)  # noqa: E731
+    arrs = [i32(ms), i32(ns), i64(coff), i32(beg), i32(k), i64(ao), i32(la), i32(at), i64(bo), i32(lb), i32(bt)]
+    alpha = np.ascontiguousarray(al, dtype=np.float64)
+    ptrs = [x.ctypes.data_as(_L if x.dtype == np.int64 else _I) for x in arrs]
+    code = lib().dmrg_grouped_gemm(int(precision), len(ms), *ptrs, alpha.ctypes.data_as(_D), _ptr(a), _ptr(b),
+                                   _ptr(c), _stream(stream))
+    _check(code, None)

@@ -1,0 +1,30 @@
+// Functions of bond.cu / solver.cu shared with the C-ABI layer.
+#pragma once
+
+#include "plan.h"
+
+namespace dmrg {
+
+void form_interms(Plan& P, Interms& im, const Block* blocks[2], double*& d_int, int64_t& n_int,
+                  double& flops);
+void ensure_ident(Plan& P, int n);
+void ensure_scratch(Plan& P, int64_t n);
+int64_t scratch_cap(const Plan& P);
+std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end);
+Basis bond_basis(const Plan& P, int b, bool right_side);
+std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward);
+void ensure_env(Plan& P, int k);
+void build_layout(Plan& P, int k);
+void set_bond(Plan& P, int k);
+BufTable bond_buffers(Plan& P, const double* psi, double* out);
+void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
+void hdiag(Plan& P, double* out, cudaStream_t st);
+
+// solver.cu
+dmrg_status davidson(Plan& P, double* psi, int n_roots, double tol, int max_iter, int precond,
+                     double* energies, int* iters);
+void decimate(Plan& P, const double* psi, int n_roots, int D, bool forward, double* discarded);
+void two_site_guess(Plan& P, double* out);
+dmrg_status sweep(Plan& P, int n_sweeps, const int* D_schedule, double* energies, double* discarded);
+
+}  // namespace dmrg

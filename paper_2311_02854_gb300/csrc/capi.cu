@@ -1,0 +1,341 @@
+// C-ABI of libdmrg (declared in include/dmrg.h).  Every entry point catches
+// exceptions and returns a status code; nothing aborts.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "bond.h"
+
+using namespace dmrg;
+
+struct dmrg_plan_s {
+    Plan P;
+};
+
+namespace {
+std::string g_last_error;
+std::mutex g_err_mu;
+
+dmrg_status fail(dmrg_plan_t plan, dmrg_status code, const std::string& msg) {
+    if (plan) plan->P.last_error = msg;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_last_error = msg;
+    return code;
+}
+
+template <class F>
+dmrg_status guarded(dmrg_plan_t plan, F&& f) {
+    try {
+        return f();
+    } catch (const Error& e) {
+        return fail(plan, e.code, e.what());
+    } catch (const std::exception& e) {
+        return fail(plan, DMRG_EINVAL, e.what());
+    }
+}
+
+cudaStream_t pick(dmrg_plan_t plan, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    plan->P.stream = s;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dmrg_default_options(dmrg_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = DMRG_FP64;
+    o->n_roots = 1;
+    o->tol = 1e-6;
+    o->max_iter = 200;
+    o->max_space = 0;
+    o->precond = DMRG_PRECOND_JACOBI;
+    o->fp64_final = 1;
+    o->mem_budget = 0;
+    o->scratch_bytes = 0;
+    o->keep_envs = 0;
+    o->verbose = 0;
+}
+
+const char* dmrg_version(void) {
+    return "libdmrg 0.1 (sm_103a; FP64 segmented grouped GEMM)";
+}
+
+dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_core, int K, int N, int twoS,
+                      int D, const dmrg_options* opt, const char* mps_path, dmrg_plan_t* out) {
+    if (!out) return fail(nullptr, DMRG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!h || !chol || n_chol <= 0 || K < 2 || K > 512 || N < 0 || N > 2 * K || D < 1)
+        return fail(nullptr, DMRG_EINVAL, "bad sizes");
+    if (((N + twoS) & 1) || std::abs(twoS) > std::min(N, 2 * K - N))
+        return fail(nullptr, DMRG_EINVAL, "inconsistent N / 2Sz");
+    if (!mps_path) return fail(nullptr, DMRG_EINVAL, "an MPS file is required");
+    for (int64_t i = 0; i < (int64_t)K * K; ++i)
+        if (!std::isfinite(h[i])) return fail(nullptr, DMRG_ENUMERIC, "non-finite one-electron integral");
+    for (int64_t i = 0; i < (int64_t)n_chol * K * K; ++i)
+        if (!std::isfinite(chol[i])) return fail(nullptr, DMRG_ENUMERIC, "non-finite Cholesky vector");
+    auto* plan = new dmrg_plan_s();
+    dmrg_status st = guarded(plan, [&]() -> dmrg_status {
+        Plan& P = plan->P;
+        if (opt) P.opt = *opt;
+        else dmrg_default_options(&P.opt);
+        if (P.opt.precision != DMRG_FP64)
+            throw Error(DMRG_EINVAL, "precision mode not available in this build");
+        P.K = K;
+        P.N = N;
+        P.twoS = twoS;
+        P.D = D;
+        P.n_so = 2 * K;
+        P.tot = QN(N, twoS);
+        P.I.K = K;
+        P.I.e_core = e_core;
+        P.I.h.assign(h, h + (int64_t)K * K);
+        std::string err;
+        if (!P.mps.read(mps_path, err)) throw Error(DMRG_EIO, err);
+        if (P.mps.K != K || P.mps.N != N || P.mps.twoS != twoS)
+            throw Error(DMRG_EINVAL, "MPS file does not match K / N / 2Sz");
+        if (P.mps.bonds[0].size() != 1 || P.mps.bonds[K].size() != 1 || P.mps.bonds[K][0][0] != N ||
+            P.mps.bonds[K][0][1] != twoS)
+            throw Error(DMRG_EINVAL, "MPS boundary sectors do not match the quantum numbers");
+        size_t freeb = 0, totb = 0;
+        DMRG_CHECK_CUDA(cudaMemGetInfo(&freeb, &totb));
+        P.budget = P.opt.mem_budget > 0 ? P.opt.mem_budget : (int64_t)(0.9 * (double)freeb);
+        // (pq|rs) = sum_X L[X][pq] L[X][rs] on the device
+        const int64_t K2 = (int64_t)K * K;
+        double* dL = P.alloc(n_chol * K2);
+        double* dE = P.alloc(K2 * K2);
+        DMRG_CHECK_CUDA(cudaMemcpy(dL, chol, n_chol * K2 * 8, cudaMemcpyHostToDevice));
+        WorkList wl;
+        Seg s{};
+        s.a_off = 0;
+        s.lda = (int)K2;
+        s.a_tr = 1;  // A(pq, X) = L[X][pq]
+        s.b_off = 0;
+        s.ldb = (int)K2;
+        s.b_tr = 0;  // B(X, rs) = L[X][rs]
+        s.k = n_chol;
+        s.a_buf = 0;
+        s.b_buf = 0;
+        s.alpha = 1.0;
+        wl.add_block(0, 1, (int)K2, (int)K2, (int)K2, {s}, TILE_STORE);
+        wl.upload(nullptr);
+        BufTable bt{};
+        bt.p[0] = dL;
+        bt.p[1] = dE;
+        launch_seg_gemm_f64(wl, bt, 1, nullptr);
+        P.I.eri.resize(K2 * K2);
+        DMRG_CHECK_CUDA(cudaMemcpy(P.I.eri.data(), dE, K2 * K2 * 8, cudaMemcpyDeviceToHost));
+        wl.release();
+        P.free(dL, n_chol * K2);
+        P.free(dE, K2 * K2);
+        P.left.resize(K + 1);
+        P.right.resize(K + 1);
+        return DMRG_OK;
+    });
+    if (st != DMRG_OK) {
+        delete plan;
+        return st;
+    }
+    *out = plan;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_set_bond(dmrg_plan_t plan, int k, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    return guarded(plan, [&]() {
+        pick(plan, stream);
+        set_bond(plan->P, k);
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_layout(dmrg_plan_t plan, int64_t* dim, int* n_sectors, int64_t* offsets, int* qn) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    Plan& P = plan->P;
+    if (P.bond < 1) return fail(plan, DMRG_EINVAL, "no current bond");
+    if (dim) *dim = P.dim;
+    if (n_sectors) *n_sectors = (int)P.layout.size();
+    const auto& bl = P.mps.bonds[P.bond - 1];
+    for (size_t i = 0; i < P.layout.size(); ++i) {
+        const Plan::Sector& s = P.layout[i];
+        if (offsets) offsets[i] = s.off;
+        if (qn) {
+            qn[6 * i + 0] = bl[s.il][0];
+            qn[6 * i + 1] = bl[s.il][1];
+            qn[6 * i + 2] = s.y / 4;
+            qn[6 * i + 3] = s.y % 4;
+            qn[6 * i + 4] = s.dl;
+            qn[6 * i + 5] = s.dr;
+        }
+    }
+    if (offsets) offsets[P.layout.size()] = P.dim;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_sigma(dmrg_plan_t plan, const double* psi, double* sig, int nvec, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || !sig) return fail(plan, DMRG_EINVAL, "NULL vector");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+        sigma(P, psi, sig, nvec, st);
+        cudaEventRecord(e1, st);
+        DMRG_CHECK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        P.stats.sigma_ms_last = ms;
+        P.stats.ms_gemm += ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_sigma_host(dmrg_plan_t plan, const double* psi, double* sig, int nvec, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || !sig || nvec < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
+        int64_t need = 2 * (int64_t)nvec * P.dim;
+        if (need > P.n_io) {
+            P.free(P.d_io, P.n_io);
+            P.n_io = need;
+            P.d_io = P.alloc(need);
+        }
+        double* dpsi = P.d_io;
+        double* dsig = P.d_io + (int64_t)nvec * P.dim;
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(dpsi, psi, (size_t)nvec * P.dim * 8, cudaMemcpyHostToDevice, st));
+        sigma(P, dpsi, dsig, nvec, st);
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(sig, dsig, (size_t)nvec * P.dim * 8, cudaMemcpyDeviceToHost, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_hdiag(dmrg_plan_t plan, double* diag, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!diag) return fail(plan, DMRG_EINVAL, "NULL vector");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        hdiag(plan->P, diag, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi, int n_roots, double tol, int max_iter, int precond,
+                          double* energies, int* iters, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || !energies || tol <= 0 || max_iter < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        pick(plan, stream);
+        return davidson(plan->P, psi, n_roots, tol, max_iter, precond, energies, iters);
+    });
+}
+
+dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi, int n_roots, int D, int forward, double* discarded,
+                          double* next_psi, int64_t* next_dim, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || n_roots < 1 || D < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        int64_t cap = next_dim ? *next_dim : 0;
+        decimate(P, psi, n_roots, D, forward != 0, discarded);
+        if (next_dim) *next_dim = P.dim;
+        if (next_psi && cap >= P.dim)
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(next_psi, P.d_guess, (size_t)n_roots * P.dim * 8,
+                                            cudaMemcpyDeviceToDevice, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, double* energies, double* discarded,
+                       void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (n_sweeps < 1 || !energies) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        pick(plan, stream);
+        return sweep(plan->P, n_sweeps, D_schedule, energies, discarded);
+    });
+}
+
+dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path) {
+    if (!plan || !path) return fail(plan, DMRG_EINVAL, "bad arguments");
+    if (!plan->P.mps.write(path)) return fail(plan, DMRG_EIO, std::string("cannot write ") + path);
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_stats(dmrg_plan_t plan, dmrg_stats_t* out) {
+    if (!plan || !out) return fail(plan, DMRG_EINVAL, "bad arguments");
+    plan->P.stats.kernel_launches = launch_counter();
+    plan->P.stats.device_bytes = plan->P.dev_bytes;
+    *out = plan->P.stats;
+    return DMRG_OK;
+}
+
+const char* dmrg_last_error(dmrg_plan_t plan) {
+    if (plan) return plan->P.last_error.c_str();
+    return g_last_error.c_str();
+}
+
+void dmrg_destroy(dmrg_plan_t plan) {
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    delete plan;
+}
+
+dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int* n, const int64_t* c_off,
+                              const int* seg_beg, const int* k, const int64_t* a_off, const int* lda, const int* a_tr,
+                              const int64_t* b_off, const int* ldb, const int* b_tr, const double* alpha,
+                              const double* a, const double* b, double* c, void* stream) {
+    if (n_out < 0 || !m || !n || !c_off || !seg_beg || !a || !b || !c) return fail(nullptr, DMRG_EINVAL, "bad arguments");
+    if (precision != DMRG_FP64) return fail(nullptr, DMRG_EINVAL, "precision mode not available in this build");
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        WorkList wl;
+        for (int o = 0; o < n_out; ++o) {
+            std::vector<Seg> segs;
+            for (int s = seg_beg[o]; s < seg_beg[o + 1]; ++s) {
+                Seg g{};
+                g.a_off = a_off[s];
+                g.b_off = b_off[s];
+                g.k = k[s];
+                g.lda = lda[s];
+                g.ldb = ldb[s];
+                g.a_tr = (uint8_t)(a_tr[s] != 0);
+                g.b_tr = (uint8_t)(b_tr[s] != 0);
+                g.a_buf = 0;
+                g.b_buf = 1;
+                g.alpha = alpha[s];
+                if (g.k < 0 || g.lda < 1 || g.ldb < 1) return fail(nullptr, DMRG_EINVAL, "bad segment");
+                segs.push_back(g);
+            }
+            if (m[o] < 0 || n[o] < 0) return fail(nullptr, DMRG_EINVAL, "bad block size");
+            wl.add_block(c_off[o], 2, m[o], n[o], n[o], segs, TILE_STORE);
+        }
+        wl.upload(st);
+        BufTable bt{};
+        bt.p[0] = const_cast<double*>(a);
+        bt.p[1] = const_cast<double*>(b);
+        bt.p[2] = c;
+        launch_seg_gemm_f64(wl, bt, 1, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        wl.release();
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(nullptr, e.code, e.what());
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// Runtime of libdmrg: MPS input/output, device memory, lowering of block
+// products onto the segmented GEMM, environments (renormalisation, Eq.
+// Renorm), the bond's intermediates and sigma (Eq. Sigma), diag(H_eff).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <fstream>
+
+#include "plan.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------------------
+// MPS file (layout documented in include/dmrg.h / synthetic_inputs.write_mps)
+// ---------------------------------------------------------------------------
+
+bool MPSHost::read(const std::string& path, std::string& err) {
+    std::ifstream f(path, std::ios::binary);
+    if (!f) {
+        err = "cannot open MPS file " + path;
+        return false;
+    }
+    char magic[8];
+    f.read(magic, 8);
+    if (!f || std::memcmp(magic, "DMRGMPS1", 8) != 0) {
+        err = "not an MPS file: " + path;
+        return false;
+    }
+    int32_t hdr[4];
+    f.read((char*)hdr, sizeof(hdr));
+    K = hdr[0];
+    N = hdr[1];
+    twoS = hdr[2];
+    center = hdr[3];
+    if (K < 2 || K > 512) {
+        err = "bad K in MPS file";
+        return false;
+    }
+    bonds.assign(K + 1, {});
+    for (int b = 0; b <= K; ++b) {
+        int32_t n;
+        f.read((char*)&n, 4);
+        if (!f || n < 0 || n > 100000) {
+            err = "bad bond table in MPS file";
+            return false;
+        }
+        for (int i = 0; i < n; ++i) {
+            int32_t s[3];
+            f.read((char*)s, 12);
+            bonds[b].push_back({s[0], s[1], s[2]});
+        }
+    }
+    sites.assign(K + 1, {});
+    for (int k = 1; k <= K; ++k) {
+        int32_t nb;
+        f.read((char*)&nb, 4);
+        if (!f || nb < 0) {
+            err = "bad site table in MPS file";
+            return false;
+        }
+        for (int i = 0; i < nb; ++i) {
+            int32_t key[3];
+            f.read((char*)key, 12);
+            if (!f || key[0] < 0 || key[0] >= (int)bonds[k - 1].size() || key[2] < 0 ||
+                key[2] >= (int)bonds[k].size() || key[1] < 0 || key[1] > 3) {
+                err = "bad block key in MPS file";
+                return false;
+            }
+            int64_t cnt = (int64_t)bonds[k - 1][key[0]][2] * bonds[k][key[2]][2];
+            std::vector<double> data(cnt);
+            f.read((char*)data.data(), cnt * 8);
+            if (!f) {
+                err = "truncated MPS file";
+                return false;
+            }
+            sites[k][{key[0], key[1], key[2]}] = std::move(data);
+        }
+    }
+    return true;
+}
+
+bool MPSHost::write(const std::string& path) const {
+    std::ofstream f(path, std::ios::binary);
+    if (!f) return false;
+    f.write("DMRGMPS1", 8);
+    int32_t hdr[4] = {K, N, twoS, center};
+    f.write((const char*)hdr, sizeof(hdr));
+    for (int b = 0; b <= K; ++b) {
+        int32_t n = (int32_t)bonds[b].size();
+        f.write((const char*)&n, 4);
+        for (auto& s : bonds[b]) {
+            int32_t v[3] = {s[0], s[1], s[2]};
+            f.write((const char*)v, 12);
+        }
+    }
+    for (int k = 1; k <= K; ++k) {
+        // canonical order: il, n, matching ir
+        std::vector<std::pair<std::array<int, 3>, const std::vector<double>*>> blocks;
+        std::map<std::pair<int, int>, int> ridx;
+        for (int i = 0; i < (int)bonds[k].size(); ++i) ridx[{bonds[k][i][0], bonds[k][i][1]}] = i;
+        for (int il = 0; il < (int)bonds[k - 1].size(); ++il)
+            for (int n = 0; n < 4; ++n) {
+                auto it = ridx.find({bonds[k - 1][il][0] + kSiteQN[n].n, bonds[k - 1][il][1] + kSiteQN[n].s});
+                if (it == ridx.end()) continue;
+                auto bt = sites[k].find({il, n, it->second});
+                blocks.push_back({{il, n, it->second}, bt == sites[k].end() ? nullptr : &bt->second});
+            }
+        int32_t nb = (int32_t)blocks.size();
+        f.write((const char*)&nb, 4);
+        for (auto& b : blocks) {
+            int32_t key[3] = {b.first[0], b.first[1], b.first[2]};
+            f.write((const char*)key, 12);
+            int64_t cnt = (int64_t)bonds[k - 1][key[0]][2] * bonds[k][key[2]][2];
+            if (b.second) {
+                f.write((const char*)b.second->data(), cnt * 8);
+            } else {
+                std::vector<double> z(cnt, 0.0);
+                f.write((const char*)z.data(), cnt * 8);
+            }
+        }
+    }
+    return (bool)f;
+}
+
+// ---------------------------------------------------------------------------
+// Device memory
+// ---------------------------------------------------------------------------
+
+double* Plan::alloc(int64_t n) {
+    if (n <= 0) return nullptr;
+    int64_t bytes = n * 8;
+    DMRG_REQUIRE(budget <= 0 || dev_bytes + bytes <= budget, DMRG_ENOMEM,
+                 "device budget exceeded (" + std::to_string((dev_bytes + bytes) >> 20) + " MiB)");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(bytes >> 20) + " MiB failed");
+    }
+    dev_bytes += bytes;
+    stats.device_bytes = dev_bytes;
+    return (double*)p;
+}
+
+void Plan::free(double*& p, int64_t n) {
+    if (p) {
+        cudaFree(p);
+        dev_bytes -= n * 8;
+        stats.device_bytes = dev_bytes;
+    }
+    p = nullptr;
+}
+
+Plan::~Plan() {
+    for (auto& b : left)
+        if (b && b->d) free(b->d, b->n);
+    for (auto& b : right)
+        if (b && b->d) free(b->d, b->n);
+    free(d_interm, n_interm);
+    free(d_scratch, n_scratch);
+    free(d_ident, (int64_t)ident_n * ident_n);
+    free(d_wcoef, n_wcoef);
+    free(d_io, n_io);
+    free(d_dav, n_dav);
+    free(d_guess, n_guess);
+    sigma_pl.release();
+    hdiag_pl.release();
+}
+
+// ---------------------------------------------------------------------------
+// Lowering of three-factor products
+// ---------------------------------------------------------------------------
+
+void ProductList::clear() {
+    release();
+    outs.clear();
+    cs.clear();
+    chunks.clear();
+    flops = 0.0;
+    scratch_elems = 0;
+}
+
+void ProductList::release() {
+    for (auto& c : chunks) {
+        c.first.release();
+        c.second.release();
+    }
+}
+
+static Seg make_seg(const View& A, const View& B, int k, double alpha) {
+    Seg s{};
+    s.a_off = A.off;
+    s.b_off = B.off;
+    s.k = k;
+    s.lda = A.ld;
+    s.ldb = B.ld;
+    s.a_buf = (uint8_t)A.buf;
+    s.b_buf = (uint8_t)B.buf;
+    s.a_tr = A.tr;
+    s.b_tr = B.tr;
+    s.alpha = alpha;
+    return s;
+}
+
+void ProductList::lower(int8_t sbuf, int8_t ibuf, int ild, int64_t cap, int64_t kchunk) {
+    release();
+    chunks.clear();
+    flops = 0.0;
+    scratch_elems = 0;
+    size_t i = 0;
+    auto ident_view = [&](void) {
+        View v;
+        v.buf = ibuf;
+        v.off = 0;
+        v.ld = ild;
+        return v;
+    };
+    while (i < cs.size()) {
+        WorkList p1, p2;
+        std::map<int, std::vector<Seg>> segs;
+        std::vector<int> order;
+        int64_t used = 0;
+        for (; i < cs.size(); ++i) {
+            const Contrib& c = cs[i];
+            int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
+            int64_t need = 0;
+            bool pq_first = true;
+            if (nreal == 3) {
+                double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                pq_first = cost_pq <= cost_qr;
+                need = pq_first ? (int64_t)c.m * c.k2 : (int64_t)c.k1 * c.n;
+                need = round_up(need, 4);
+                if (used + need > cap && used > 0) break;
+                flops += std::min(cost_pq, cost_qr);
+            }
+            if (!segs.count(c.out)) order.push_back(c.out);
+            std::vector<Seg>& sv = segs[c.out];
+            if (nreal == 3) {
+                View T;
+                T.buf = sbuf;
+                T.off = used;
+                if (pq_first) {
+                    T.ld = c.k2;
+                    std::vector<Seg> one{make_seg(c.P, c.Q, c.k1, 1.0)};
+                    p1.add_block(used, sbuf, c.m, c.k2, c.k2, one, TILE_STORE);
+                    sv.push_back(make_seg(T, c.R, c.k2, c.alpha));
+                } else {
+                    T.ld = c.n;
+                    std::vector<Seg> one{make_seg(c.Q, c.R, c.k2, 1.0)};
+                    p1.add_block(used, sbuf, c.k1, c.n, c.n, one, TILE_STORE);
+                    sv.push_back(make_seg(c.P, T, c.k1, c.alpha));
+                }
+                used += need;
+            } else if (nreal == 2) {
+                if (c.P.ident) sv.push_back(make_seg(c.Q, c.R, c.k2, c.alpha));
+                else if (c.R.ident) sv.push_back(make_seg(c.P, c.Q, c.k1, c.alpha));
+                else sv.push_back(make_seg(c.P, c.R, c.k1, c.alpha));
+                flops += 2.0 * c.m * c.n * (c.P.ident ? c.k2 : c.k1);
+            } else {
+                const View& F = !c.P.ident ? c.P : (!c.Q.ident ? c.Q : c.R);
+                if (nreal == 1) sv.push_back(make_seg(F, ident_view(), c.n, c.alpha));
+                else sv.push_back(make_seg(ident_view(), ident_view(), c.n, c.alpha));
+                flops += 2.0 * c.m * c.n;
+            }
+        }
+        for (int o : order) {
+            const OutBlock& ob = outs[o];
+            p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], TILE_ATOMIC, kchunk);
+        }
+        scratch_elems = std::max(scratch_elems, used);
+        chunks.emplace_back(std::move(p1), std::move(p2));
+    }
+}
+
+void ProductList::upload(cudaStream_t st) {
+    for (auto& c : chunks) {
+        c.first.upload(st);
+        c.second.upload(st);
+    }
+}
+
+void ProductList::run(const BufTable& bt, int nvec, cudaStream_t st) {
+    for (auto& c : chunks) {
+        launch_seg_gemm_f64(c.first, bt, nvec, st);
+        launch_seg_gemm_f64(c.second, bt, nvec, st);
+    }
+}
+
+}  // namespace dmrg

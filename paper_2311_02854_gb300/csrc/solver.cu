@@ -1,0 +1,704 @@
+// Davidson eigensolver (Sec. 2.1, Davidson 1975), decimation by the
+// (state-averaged) reduced density matrix (Sec. 2.1), and the two-dot sweep
+// (Sec. 2.3, Fig. flowchart).  All vector arithmetic runs on the device in
+// FP64; the host keeps only the small subspace matrix and scalars.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "bond.h"
+
+namespace dmrg {
+
+namespace {
+enum : int8_t { BUF_L = 0, BUF_R = 1, BUF_INT = 2, BUF_PSI = 3, BUF_SCR = 4, BUF_ID = 5, BUF_OUT = 6, BUF_W = 7 };
+
+double host_dot(Plan& P, const double* x, const double* y, int64_t n, double* d_out, double* d_work) {
+    dev_dots(x, n, 1, y, n, d_out, d_work, P.stream);
+    double r = 0.0;
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(&r, d_out, 8, cudaMemcpyDeviceToHost, P.stream));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+    return r;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Davidson
+// ---------------------------------------------------------------------------
+
+dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int precond,
+                     double* energies, int* iters) {
+    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
+    DMRG_REQUIRE(nr >= 1 && nr <= 16, DMRG_EINVAL, "n_roots must be in 1..16");
+    const int64_t n = P.dim;
+    DMRG_REQUIRE(n >= nr, DMRG_EINVAL, "fewer states than roots at this bond");
+    int ms = P.opt.max_space > 0 ? P.opt.max_space : 20 * nr;
+    ms = std::max(ms, 3 * nr);
+    ms = (int)std::min<int64_t>(ms, n);
+    const int64_t need = (int64_t)(2 * ms + 3 * nr + 2) * n + (int64_t)ms * 260 + 3LL * ms * ms + 4 * ms;
+    if (need > P.n_dav) {
+        P.free(P.d_dav, P.n_dav);
+        P.n_dav = need;
+        P.d_dav = P.alloc(need);
+    }
+    double* V = P.d_dav;
+    double* W = V + (int64_t)ms * n;
+    double* X = W + (int64_t)ms * n;
+    double* WY = X + (int64_t)nr * n;
+    double* T = WY + (int64_t)nr * n;
+    double* hd = T + (int64_t)nr * n;
+    double* tmp = hd + n;
+    double* dwork = tmp + n;
+    double* dco = dwork + (int64_t)ms * 256;
+    double* dG = dco + 4 * ms;
+    double* dGv = dG + (int64_t)ms * ms;
+    double* dev = dGv + (int64_t)ms * ms;
+    cudaStream_t st = P.stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+
+    hdiag(P, hd, st);
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(T, psi, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> G((size_t)ms * ms, 0.0);
+    std::vector<double> theta(nr, 0.0), rnorm(nr, 0.0);
+    int m = 0, nnew = nr, it = 0;
+    bool conv = false;
+    EigJob job;
+    EigJob* d_job = nullptr;
+    DMRG_CHECK_CUDA(cudaMalloc(&d_job, sizeof(EigJob)));
+    std::vector<double> Gv;
+    std::vector<int> order;
+    while (true) {
+        // orthonormalise the new directions (classical Gram-Schmidt, twice)
+        int added = 0;
+        for (int t = 0; t < nnew; ++t) {
+            double* x = T + (int64_t)t * n;
+            for (int pass = 0; pass < 2; ++pass) {
+                int mm = m + added;
+                if (mm == 0) break;
+                dev_dots(V, n, mm, x, n, dco, dwork, st);
+                dev_combine(V, n, mm, dco, n, tmp, st);
+                dev_axpby(-1.0, tmp, 1.0, x, n, st);
+            }
+            double nrm2 = host_dot(P, x, x, n, dco, dwork);
+            if (!(nrm2 == nrm2) || std::isinf(nrm2)) {
+                cudaFree(d_job);
+                throw Error(DMRG_ENUMERIC, "non-finite Davidson direction");
+            }
+            double nrm = std::sqrt(nrm2);
+            if (nrm > 1e-10) {
+                double* dst = V + (int64_t)(m + added) * n;
+                dev_axpby(1.0 / nrm, x, 0.0, dst, n, st);
+                ++added;
+            }
+        }
+        // fewer independent guesses than roots: add hashed perturbations of the first vector
+        for (int tries = 0; m + added < nr && tries < 8 * nr; ++tries) {
+            double* x = T;
+            if (m + added > 0)
+                DMRG_CHECK_CUDA(cudaMemcpyAsync(x, V, n * 8, cudaMemcpyDeviceToDevice, st));
+            else
+                dev_fill(x, 0.0, n, st);
+            dev_perturb(x, n, 7919u + (uint32_t)tries, 1.0, st);
+            for (int pass = 0; pass < 2 && m + added > 0; ++pass) {
+                dev_dots(V, n, m + added, x, n, dco, dwork, st);
+                dev_combine(V, n, m + added, dco, n, tmp, st);
+                dev_axpby(-1.0, tmp, 1.0, x, n, st);
+            }
+            double nrm = std::sqrt(std::max(0.0, host_dot(P, x, x, n, dco, dwork)));
+            if (nrm > 1e-10) {
+                dev_axpby(1.0 / nrm, x, 0.0, V + (int64_t)(m + added) * n, n, st);
+                ++added;
+            }
+        }
+        if (added == 0) break;
+        sigma(P, V + (int64_t)m * n, W + (int64_t)m * n, added, st);
+        for (int j = m; j < m + added; ++j) {
+            dev_dots(V, n, m + added, W + (int64_t)j * n, n, dco, dwork, st);
+            std::vector<double> col(m + added);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(col.data(), dco, (m + added) * 8, cudaMemcpyDeviceToHost, st));
+            DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i < m + added; ++i) {
+                G[(size_t)i * ms + j] = col[i];
+                G[(size_t)j * ms + i] = col[i];
+            }
+        }
+        m += added;
+        ++it;
+        // Ritz problem on the device (Jacobi)
+        std::vector<double> Gs((size_t)m * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) Gs[(size_t)i * m + j] = 0.5 * (G[(size_t)i * ms + j] + G[(size_t)j * ms + i]);
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(dG, Gs.data(), (size_t)m * m * 8, cudaMemcpyHostToDevice, st));
+        job.A = dG;
+        job.V = dGv;
+        job.w = dev;
+        job.n = m;
+        job.lda = m;
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(d_job, &job, sizeof(EigJob), cudaMemcpyHostToDevice, st));
+        dev_jacobi_eigh_batched(d_job, 1, 40, st);
+        std::vector<double> w(m);
+        Gv.assign((size_t)m * m, 0.0);
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(w.data(), dev, m * 8, cudaMemcpyDeviceToHost, st));
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(Gv.data(), dGv, (size_t)m * m * 8, cudaMemcpyDeviceToHost, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        order.resize(m);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] < w[b]; });
+        bool all = true;
+        for (int i = 0; i < nr; ++i) {
+            int c = order[i];
+            theta[i] = w[c];
+            std::vector<double> y(m);
+            for (int r = 0; r < m; ++r) y[r] = Gv[(size_t)r * m + c];
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(dco, y.data(), m * 8, cudaMemcpyHostToDevice, st));
+            double* xi = X + (int64_t)i * n;
+            double* wy = WY + (int64_t)i * n;
+            dev_combine(V, n, m, dco, n, xi, st);
+            dev_combine(W, n, m, dco, n, wy, st);
+            double* ri = T + (int64_t)i * n;
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(ri, wy, n * 8, cudaMemcpyDeviceToDevice, st));
+            dev_axpby(-theta[i], xi, 1.0, ri, n, st);
+            rnorm[i] = std::sqrt(std::max(0.0, host_dot(P, ri, ri, n, dco + 2 * ms, dwork)));
+            if (!(rnorm[i] == rnorm[i])) {
+                cudaFree(d_job);
+                throw Error(DMRG_ENUMERIC, "non-finite Davidson residual");
+            }
+            all = all && rnorm[i] <= tol;
+        }
+        if (P.opt.verbose)
+            fprintf(stderr, "[dmrg] davidson it=%d m=%d theta0=%.12f |r0|=%.3e\n", it, m, theta[0], rnorm[0]);
+        if (all) {
+            conv = true;
+            break;
+        }
+        if (it >= max_iter) break;
+        // corrections
+        for (int i = 0; i < nr; ++i) {
+            double* ri = T + (int64_t)i * n;
+            dev_jacobi_precond(ri, hd, theta[i], ri, n, st);
+        }
+        if (precond == DMRG_PRECOND_MLP) P.stats.precond_fallbacks += nr;
+        nnew = nr;
+        if (m + nr > ms) {  // restart with the Ritz vectors
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(V, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(W, WY, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+            std::fill(G.begin(), G.end(), 0.0);
+            for (int i = 0; i < nr; ++i) G[(size_t)i * ms + i] = theta[i];
+            m = nr;
+        }
+    }
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(psi, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+    cudaEventRecord(e1, st);
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    float ms_ = 0.f;
+    cudaEventElapsedTime(&ms_, e0, e1);
+    P.stats.ms_davidson += ms_;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_job);
+    for (int i = 0; i < nr; ++i) energies[i] = theta[i] + P.I.e_core;
+    if (iters) *iters = it;
+    P.stats.davidson_iters_last = it;
+    return conv ? DMRG_OK : DMRG_ENOTCONV;
+}
+
+// ---------------------------------------------------------------------------
+// Decimation
+// ---------------------------------------------------------------------------
+
+namespace {
+struct Comp {
+    int a, b;  // forward: (il, c1) ; backward: (c2, ir)
+    int dim;
+    int64_t off;
+};
+struct Group {
+    QN q;
+    std::vector<Comp> rows;
+    std::map<std::pair<int, int>, int> rindex;
+    int n = 0;
+    int64_t rho_off = 0;
+    std::vector<double> w;
+    std::vector<int> kept;  // column indices of V_q
+};
+}  // namespace
+
+void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double* discarded) {
+    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
+    const int k = P.bond, K = P.K;
+    DMRG_REQUIRE(forward ? (k + 1 <= K - 1) : (k - 1 >= 1), DMRG_EINVAL, "cannot move past the chain end");
+    cudaStream_t st = P.stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    const auto bl = P.mps.bonds[k - 1];
+    const auto br = P.mps.bonds[k + 1];
+    // groups by the label of bond k
+    std::map<QN, Group> groups;
+    for (const Plan::Sector& s : P.layout) {
+        int c1 = s.y / 4, c2 = s.y % 4;
+        QN q = QN(bl[s.il][0], bl[s.il][1]) + kSiteQN[c1];
+        Group& g = groups[q];
+        g.q = q;
+        std::pair<int, int> key = forward ? std::make_pair(s.il, c1) : std::make_pair(c2, s.ir);
+        if (!g.rindex.count(key)) {
+            g.rindex[key] = (int)g.rows.size();
+            g.rows.push_back({key.first, key.second, forward ? s.dl : s.dr, (int64_t)g.n});
+            g.n += forward ? s.dl : s.dr;
+        }
+    }
+    int64_t rho_tot = 0;
+    for (auto& kv : groups) {
+        kv.second.rho_off = rho_tot;
+        rho_tot += (int64_t)kv.second.n * kv.second.n;
+    }
+    double* d_rho = P.alloc(2 * rho_tot + rho_tot / 1 + 64);
+    double* d_vec = d_rho + rho_tot;
+    double* d_w = d_vec + rho_tot;
+    // rho_q = (1/nr) sum_roots M M^T (forward) or M^T M (backward)
+    WorkList wl;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        std::map<std::pair<int, int>, std::vector<Seg>> blk;  // (row comp, col comp) -> segs
+        // list sectors of this group
+        std::vector<const Plan::Sector*> secs;
+        for (const Plan::Sector& s : P.layout) {
+            QN q = QN(bl[s.il][0], bl[s.il][1]) + kSiteQN[s.y / 4];
+            if (q == g.q) secs.push_back(&s);
+        }
+        for (const Plan::Sector* a : secs)
+            for (const Plan::Sector* b : secs) {
+                int ra, rb;
+                Seg sg{};
+                if (forward) {
+                    if (a->y % 4 != b->y % 4 || a->ir != b->ir) continue;  // same column comp (c2, ir)
+                    ra = g.rindex[{a->il, a->y / 4}];
+                    rb = g.rindex[{b->il, b->y / 4}];
+                    sg.a_off = a->off;
+                    sg.lda = a->dr;
+                    sg.a_tr = 0;
+                    sg.b_off = b->off;
+                    sg.ldb = b->dr;
+                    sg.b_tr = 1;
+                    sg.k = a->dr;
+                } else {
+                    if (a->il != b->il || a->y / 4 != b->y / 4) continue;  // same column comp (il, c1)
+                    ra = g.rindex[{a->y % 4, a->ir}];
+                    rb = g.rindex[{b->y % 4, b->ir}];
+                    sg.a_off = a->off;
+                    sg.lda = a->dr;
+                    sg.a_tr = 1;
+                    sg.b_off = b->off;
+                    sg.ldb = b->dr;
+                    sg.b_tr = 0;
+                    sg.k = a->dl;
+                }
+                sg.a_buf = BUF_PSI;
+                sg.b_buf = BUF_PSI;
+                sg.alpha = 1.0 / nr;
+                for (int v = 0; v < nr; ++v) {
+                    Seg s2 = sg;
+                    s2.a_off += (int64_t)v * P.dim;
+                    s2.b_off += (int64_t)v * P.dim;
+                    blk[{ra, rb}].push_back(s2);
+                }
+            }
+        for (auto& bk : blk) {
+            const Comp& ca = g.rows[bk.first.first];
+            const Comp& cb = g.rows[bk.first.second];
+            wl.add_block(g.rho_off + ca.off * g.n + cb.off, BUF_OUT, ca.dim, cb.dim, g.n, bk.second, TILE_STORE);
+        }
+    }
+    DMRG_CHECK_CUDA(cudaMemsetAsync(d_rho, 0, rho_tot * 8, st));
+    wl.upload(st);
+    BufTable bt{};
+    bt.p[BUF_PSI] = const_cast<double*>(psi);
+    bt.p[BUF_OUT] = d_rho;
+    launch_seg_gemm_f64(wl, bt, 1, st);
+    // eigen-decomposition of every rho_q
+    std::vector<EigJob> jobs;
+    int64_t woff = 0;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        EigJob j;
+        j.A = d_rho + g.rho_off;
+        j.V = d_vec + g.rho_off;
+        j.w = d_w + woff;
+        j.n = g.n;
+        j.lda = g.n;
+        woff += g.n;
+        jobs.push_back(j);
+        DMRG_REQUIRE(g.n <= 4096, DMRG_EINVAL, "density-matrix sector larger than 4096");
+    }
+    EigJob* d_jobs = nullptr;
+    DMRG_CHECK_CUDA(cudaMalloc(&d_jobs, jobs.size() * sizeof(EigJob)));
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(EigJob), cudaMemcpyHostToDevice, st));
+    dev_jacobi_eigh_batched(d_jobs, (int)jobs.size(), 60, st);
+    std::vector<double> hw(woff), hv(rho_tot);
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(hw.data(), d_w, woff * 8, cudaMemcpyDeviceToHost, st));
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(hv.data(), d_vec, rho_tot * 8, cudaMemcpyDeviceToHost, st));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d_jobs);
+    wl.release();
+    P.free(d_rho, 2 * rho_tot + rho_tot + 64);
+    // choose the kept states: largest weights, ties by group order then rank
+    struct Cand {
+        double w;
+        int g, rank, col;
+    };
+    std::vector<Cand> cands;
+    std::vector<Group*> glist;
+    woff = 0;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        g.w.assign(hw.begin() + woff, hw.begin() + woff + g.n);
+        woff += g.n;
+        std::vector<int> ord(g.n);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return g.w[a] > g.w[b]; });
+        for (int r = 0; r < g.n; ++r) cands.push_back({g.w[ord[r]], (int)glist.size(), r, ord[r]});
+        glist.push_back(&g);
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
+        if (a.w != b.w) return a.w > b.w;
+        if (a.g != b.g) return a.g < b.g;
+        return a.rank < b.rank;
+    });
+    double wdisc = 0.0;
+    int nkept = 0;
+    for (const Cand& c : cands) {
+        if (nkept < Dmax && c.w > 1e-28) {
+            glist[c.g]->kept.push_back(c.col);
+            ++nkept;
+        } else {
+            wdisc += std::max(c.w, 0.0);
+        }
+    }
+    if (discarded) *discarded = wdisc;
+    // new bond-k sectors (group order) and the new site tensor
+    std::vector<std::array<int, 3>> newbond;
+    std::map<std::array<int, 3>, std::vector<double>> newsite;
+    std::map<QN, int> newidx;
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        if (g.kept.empty()) continue;
+        // keep columns in descending-weight order (rank order)
+        std::stable_sort(g.kept.begin(), g.kept.end(), [&](int a, int b) { return g.w[a] > g.w[b]; });
+        newidx[g.q] = (int)newbond.size();
+        newbond.push_back({g.q.n, g.q.s, (int)g.kept.size()});
+    }
+    for (auto& kv : groups) {
+        Group& g = kv.second;
+        if (g.kept.empty()) continue;
+        const int inew = newidx[g.q];
+        const int nk = (int)g.kept.size();
+        const double* Vq = hv.data() + g.rho_off;
+        for (const Comp& c : g.rows) {
+            std::vector<double> blk((size_t)c.dim * nk);
+            for (int a = 0; a < c.dim; ++a)
+                for (int t = 0; t < nk; ++t) blk[(size_t)a * nk + t] = Vq[(size_t)(c.off + a) * g.n + g.kept[t]];
+            if (forward) {
+                newsite[{c.a, c.b, inew}] = std::move(blk);  // (il, c1, new): d_il x nk
+            } else {
+                std::vector<double> bt_((size_t)nk * c.dim);  // (new, c2, ir): nk x d_ir
+                for (int a = 0; a < c.dim; ++a)
+                    for (int t = 0; t < nk; ++t) bt_[(size_t)t * c.dim + a] = blk[(size_t)a * nk + t];
+                newsite[{inew, c.a, c.b}] = std::move(bt_);
+            }
+        }
+    }
+    // install into the MPS and drop stale environments
+    std::vector<Plan::Sector> old_layout = P.layout;
+    const int64_t old_dim = P.dim;
+    P.mps.bonds[k] = newbond;
+    if (forward) {
+        P.mps.sites[k] = newsite;
+        P.mps.center = k + 1;
+        for (int m = k; m <= K; ++m)
+            if (P.left[m]) { P.free(P.left[m]->d, P.left[m]->n); P.left[m].reset(); }
+        for (int m = 0; m <= k - 1; ++m)
+            if (P.right[m]) { P.free(P.right[m]->d, P.right[m]->n); P.right[m].reset(); }
+    } else {
+        P.mps.sites[k + 1] = newsite;
+        P.mps.center = k - 1;
+        for (int m = 0; m <= k; ++m)
+            if (P.right[m]) { P.free(P.right[m]->d, P.right[m]->n); P.right[m].reset(); }
+        for (int m = k + 1; m <= K; ++m)
+            if (P.left[m]) { P.free(P.left[m]->d, P.left[m]->n); P.left[m].reset(); }
+    }
+    // guess for the next bond: U^T Psi A[k+2] (forward) or A[k-1] Psi V (backward)
+    const int kn = forward ? k + 1 : k - 1;
+    const auto nbl = P.mps.bonds[kn - 1];
+    const auto nbr = P.mps.bonds[kn + 1];
+    std::map<std::pair<int, int>, int> ridx;
+    for (int i = 0; i < (int)nbr.size(); ++i) ridx[{nbr[i][0], nbr[i][1]}] = i;
+    struct NSec {
+        int il, y, ir;
+        int64_t off;
+        int dl, dr;
+    };
+    std::vector<NSec> nl;
+    std::map<std::pair<int, int>, int> nsec_of;
+    int64_t ndim = 0;
+    for (int il = 0; il < (int)nbl.size(); ++il)
+        for (int y = 0; y < 16; ++y) {
+            QN q = QN(nbl[il][0], nbl[il][1]) + kSiteQN[y / 4] + kSiteQN[y % 4];
+            auto it = ridx.find({q.n, q.s});
+            if (it == ridx.end()) continue;
+            nsec_of[{il, y}] = (int)nl.size();
+            nl.push_back({il, y, it->second, ndim, nbl[il][2], nbr[it->second][2]});
+            ndim += (int64_t)nbl[il][2] * nbr[it->second][2];
+        }
+    P.free(P.d_guess, P.n_guess);
+    P.n_guess = std::max<int64_t>((int64_t)nr * ndim, 1);
+    P.d_guess = P.alloc(P.n_guess);
+    P.guess_nr = nr;
+    double* next_psi = P.d_guess;
+    {
+        // device copies of the two site tensors used
+        const int sa = forward ? k : k - 1;       // U (new A[k]) or A[k-1]
+        const int sb = forward ? k + 2 : k + 1;   // A[k+2] or V (new A[k+1])
+        auto upload = [&](int site, std::map<std::array<int, 3>, int64_t>& off, int64_t& nn) {
+            int64_t tot = 0;
+            for (auto& kv : P.mps.sites[site]) {
+                off[kv.first] = tot;
+                tot += (int64_t)kv.second.size();
+            }
+            nn = std::max<int64_t>(tot, 1);
+            double* d = P.alloc(nn);
+            std::vector<double> h(nn, 0.0);
+            for (auto& kv : P.mps.sites[site]) std::copy(kv.second.begin(), kv.second.end(), h.begin() + off[kv.first]);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(d, h.data(), nn * 8, cudaMemcpyHostToDevice, st));
+            DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+            return d;
+        };
+        std::map<std::array<int, 3>, int64_t> offa, offb;
+        int64_t na = 0, nb = 0;
+        double* da = upload(sa, offa, na);
+        double* db = upload(sb, offb, nb);
+        ProductList pl;
+        for (auto& s : nl) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
+        for (const Plan::Sector& s : old_layout) {
+            const int c1 = s.y / 4, c2 = s.y % 4;
+            if (forward) {
+                // old (il, c1, c2, ir) with U(il, c1, new) and A[k+2](ir, c3, ir')
+                QN q = QN(bl[s.il][0], bl[s.il][1]) + kSiteQN[c1];
+                auto ni = newidx.find(q);
+                if (ni == newidx.end()) continue;
+                auto ua = offa.find({s.il, c1, ni->second});
+                if (ua == offa.end()) continue;
+                const int nk = newbond[ni->second][2];
+                for (int c3 = 0; c3 < 4; ++c3) {
+                    for (auto& kv : P.mps.sites[sb]) {
+                        if (kv.first[0] != s.ir || kv.first[1] != c3) continue;
+                        const int ir2 = kv.first[2];
+                        auto os = nsec_of.find({ni->second, c2 * 4 + c3});
+                        if (os == nsec_of.end()) continue;
+                        const NSec& o = nl[os->second];
+                        if (o.ir != ir2) continue;
+                        Contrib c;
+                        c.out = os->second;
+                        c.P.buf = BUF_L;
+                        c.P.off = ua->second;
+                        c.P.ld = nk;
+                        c.P.tr = true;   // U^T : nk x d_il
+                        c.Q.buf = BUF_PSI;
+                        c.Q.off = s.off;
+                        c.Q.ld = s.dr;   // Psi : d_il x d_ir
+                        c.R.buf = BUF_R;
+                        c.R.off = offb[kv.first];
+                        c.R.ld = o.dr;   // A[k+2](ir, c3, ir2) : d_ir x d_ir2
+                        c.m = nk;
+                        c.k1 = s.dl;
+                        c.k2 = s.dr;
+                        c.n = o.dr;
+                        c.alpha = 1.0;
+                        pl.cs.push_back(c);
+                    }
+                }
+            } else {
+                // old (il, c1, c2, ir) with A[k-1](il0, c0, il) and V(new, c2, ir)
+                QN q = QN(br[s.ir][0], br[s.ir][1]) - kSiteQN[c2];
+                auto ni = newidx.find(q);
+                if (ni == newidx.end()) continue;
+                auto vb = offb.find({ni->second, c2, s.ir});
+                if (vb == offb.end()) continue;
+                const int nk = newbond[ni->second][2];
+                for (auto& kv : P.mps.sites[sa]) {
+                    if (kv.first[2] != s.il) continue;
+                    const int il0 = kv.first[0], c0 = kv.first[1];
+                    auto os = nsec_of.find({il0, c0 * 4 + c1});
+                    if (os == nsec_of.end()) continue;
+                    const NSec& o = nl[os->second];
+                    if (o.ir != ni->second) continue;
+                    Contrib c;
+                    c.out = os->second;
+                    c.P.buf = BUF_L;
+                    c.P.off = offa[kv.first];
+                    c.P.ld = s.dl;    // A[k-1](il0, c0, il) : d_il0 x d_il
+                    c.Q.buf = BUF_PSI;
+                    c.Q.off = s.off;
+                    c.Q.ld = s.dr;    // Psi : d_il x d_ir
+                    c.R.buf = BUF_R;
+                    c.R.off = vb->second;
+                    c.R.ld = s.dr;
+                    c.R.tr = true;    // V^T : d_ir x nk
+                    c.m = o.dl;
+                    c.k1 = s.dl;
+                    c.k2 = s.dr;
+                    c.n = nk;
+                    c.alpha = 1.0;
+                    pl.cs.push_back(c);
+                }
+            }
+        }
+        int maxd = 1;
+        for (auto& b : nbl) maxd = std::max(maxd, b[2]);
+        for (auto& b : nbr) maxd = std::max(maxd, b[2]);
+        for (auto& b : bl) maxd = std::max(maxd, b[2]);
+        for (auto& b : br) maxd = std::max(maxd, b[2]);
+        ensure_ident(P, maxd);
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), 1 << 14);
+        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1) * nr);
+        pl.upload(st);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(next_psi, 0, (size_t)nr * ndim * 8, st));
+        BufTable b2{};
+        b2.p[BUF_L] = da;
+        b2.p[BUF_R] = db;
+        b2.p[BUF_PSI] = const_cast<double*>(psi);
+        b2.p[BUF_SCR] = P.d_scratch;
+        b2.p[BUF_ID] = P.d_ident;
+        b2.p[BUF_OUT] = next_psi;
+        b2.vstride[BUF_PSI] = old_dim;
+        b2.vstride[BUF_OUT] = ndim;
+        b2.vstride[BUF_SCR] = std::max<int64_t>(pl.scratch_elems, 1);
+        pl.run(b2, nr, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        pl.release();
+        P.free(da, na);
+        P.free(db, nb);
+    }
+    P.bond = -1;
+    cudaEventRecord(e1, st);
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    float ms_ = 0.f;
+    cudaEventElapsedTime(&ms_, e0, e1);
+    P.stats.ms_decim += ms_;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_bond(P, kn);  // renormalises the grown block and plans the next bond
+}
+
+// Two-site tensor A[k] A[k+1] of the current MPS, in the canonical layout.
+void two_site_guess(Plan& P, double* out) {
+    const int k = P.bond;
+    cudaStream_t st = P.stream;
+    const auto& bm = P.mps.bonds[k];
+    std::map<std::array<int, 3>, int64_t> offa, offb;
+    int64_t na = 0, nb = 0;
+    auto upload = [&](int site, std::map<std::array<int, 3>, int64_t>& off, int64_t& nn) {
+        int64_t tot = 0;
+        for (auto& kv : P.mps.sites[site]) {
+            off[kv.first] = tot;
+            tot += (int64_t)kv.second.size();
+        }
+        nn = std::max<int64_t>(tot, 1);
+        double* d = P.alloc(nn);
+        std::vector<double> h(nn, 0.0);
+        for (auto& kv : P.mps.sites[site]) std::copy(kv.second.begin(), kv.second.end(), h.begin() + off[kv.first]);
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(d, h.data(), nn * 8, cudaMemcpyHostToDevice, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return d;
+    };
+    double* da = upload(k, offa, na);
+    double* db = upload(k + 1, offb, nb);
+    WorkList wl;
+    for (const Plan::Sector& s : P.layout) {
+        const int c1 = s.y / 4, c2 = s.y % 4;
+        std::vector<Seg> segs;
+        for (int im = 0; im < (int)bm.size(); ++im) {
+            auto a = offa.find({s.il, c1, im});
+            auto b = offb.find({im, c2, s.ir});
+            if (a == offa.end() || b == offb.end()) continue;
+            Seg sg{};
+            sg.a_off = a->second;
+            sg.lda = bm[im][2];
+            sg.b_off = b->second;
+            sg.ldb = s.dr;
+            sg.k = bm[im][2];
+            sg.a_buf = BUF_L;
+            sg.b_buf = BUF_R;
+            sg.alpha = 1.0;
+            segs.push_back(sg);
+        }
+        wl.add_block(s.off, BUF_OUT, s.dl, s.dr, s.dr, segs, TILE_STORE);
+    }
+    wl.upload(st);
+    BufTable bt{};
+    bt.p[BUF_L] = da;
+    bt.p[BUF_R] = db;
+    bt.p[BUF_OUT] = out;
+    launch_seg_gemm_f64(wl, bt, 1, st);
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    wl.release();
+    P.free(da, na);
+    P.free(db, nb);
+}
+
+// ---------------------------------------------------------------------------
+// Sweep
+// ---------------------------------------------------------------------------
+
+dmrg_status sweep(Plan& P, int n_sweeps, const int* D_schedule, double* energies, double* discarded) {
+    DMRG_REQUIRE(P.mps.center == 1, DMRG_EINVAL, "sweeps start from an MPS centred on bond (1,2)");
+    const int K = P.K;
+    const int nr = P.opt.n_roots;
+    const int keep = P.opt.keep_envs;
+    P.opt.keep_envs = 1;
+    if (P.bond != 1) set_bond(P, 1);
+    int64_t psi_n = (int64_t)nr * P.dim;
+    double* psi = P.alloc(psi_n);
+    two_site_guess(P, psi);
+    for (int v = 1; v < nr; ++v) {
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(psi + (int64_t)v * P.dim, psi, P.dim * 8, cudaMemcpyDeviceToDevice, P.stream));
+        dev_perturb(psi + (int64_t)v * P.dim, P.dim, 1000u + v, 0.5, P.stream);
+    }
+    dmrg_status last = DMRG_OK;
+    std::vector<double> en(nr);
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        const int D = D_schedule ? D_schedule[sw] : P.D;
+        double wmax = 0.0;
+        std::vector<std::pair<int, bool>> steps;
+        for (int k = 1; k <= K - 2; ++k) steps.push_back({k, true});
+        for (int k = K - 1; k >= 2; --k) steps.push_back({k, false});
+        for (auto& step : steps) {
+            const int k = step.first;
+            if (P.bond != k) set_bond(P, k);
+            int iters = 0;
+            dmrg_status s = davidson(P, psi, nr, P.opt.tol, P.opt.max_iter, P.opt.precond, en.data(), &iters);
+            if (s == DMRG_ENOTCONV) last = s;
+            if (P.opt.verbose)
+                fprintf(stderr, "[dmrg] sweep %d bond %d %s E=%.12f iters=%d\n", sw, k, step.second ? "fwd" : "bwd",
+                        en[0], iters);
+            double w = 0.0;
+            decimate(P, psi, nr, D, step.second, &w);
+            wmax = std::max(wmax, w);
+            P.free(psi, psi_n);
+            psi = P.d_guess;
+            psi_n = P.n_guess;
+            P.d_guess = nullptr;
+            P.n_guess = 0;
+        }
+        energies[sw] = en[0];
+        if (discarded) discarded[sw] = wmax;
+    }
+    P.free(psi, psi_n);
+    P.opt.keep_envs = keep;
+    return last;
+}
+
+}  // namespace dmrg
