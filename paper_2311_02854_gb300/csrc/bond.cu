@@ -52,7 +52,7 @@ static OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r
         o.j = f->bra[pr];
         o.v.buf = buf;
         o.v.off = rowbase + f->off[pr];
-        o.v.ld = b.dim[i];
+        o.v.ld = f->ld[pr];
         o.v.tr = false;
     } else {
         int j = b.find(b.qn[i] - f->dq);
@@ -62,7 +62,7 @@ static OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r
         o.j = j;
         o.v.buf = buf;
         o.v.off = rowbase + f->off[pr];
-        o.v.ld = b.dim[j];
+        o.v.ld = f->ld[pr];
         o.v.tr = true;
     }
     o.ok = true;
@@ -276,7 +276,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                         if (oi == outidx.end()) {
                             o = (int)pl.outs.size();
                             outidx[key] = o;
-                            pl.outs.push_back({BUF_R, obase + of.off[pr], djr, dr, dr});
+                            pl.outs.push_back({BUF_R, obase + of.off[pr], djr, dr, of.ld[pr]});
                         } else {
                             o = oi->second;
                         }
@@ -318,7 +318,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                         if (oi == outidx.end()) {
                             o = (int)pl.outs.size();
                             outidx[key] = o;
-                            pl.outs.push_back({BUF_R, obase + of.off[pr], djl, dl, dl});
+                            pl.outs.push_back({BUF_R, obase + of.off[pr], djl, dl, of.ld[pr]});
                         } else {
                             o = oi->second;
                         }

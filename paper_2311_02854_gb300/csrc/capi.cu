@@ -5,6 +5,7 @@
 #include <mutex>
 
 #include "bond.h"
+#include "tc.h"
 
 using namespace dmrg;
 
@@ -32,6 +33,92 @@ dmrg_status guarded(dmrg_plan_t plan, F&& f) {
     } catch (const std::exception& e) {
         return fail(plan, DMRG_EINVAL, e.what());
     }
+}
+
+// Tensor-core grouped GEMM on FP64 operand buffers: the operands are split
+// into bf16 pieces on the device, the product runs on tcgen05, and C is
+// accumulated in FP64.  Leading dimensions and offsets must be multiples of
+// 8 elements; segment alphas must be +1 or -1, except for single-segment
+// blocks (scaled in the epilogue).
+dmrg_status grouped_gemm_tc(int nsplit, int n_out, const int* m, const int* n, const int64_t* c_off,
+                            const int* seg_beg, const int* k, const int64_t* a_off, const int* lda,
+                            const int* a_tr, const int64_t* b_off, const int* ldb, const int* b_tr,
+                            const double* alpha, const double* a, const double* b, double* c,
+                            cudaStream_t st) {
+    int64_t ea = 8, eb = 8, ec = 0;
+    WorkList wl;
+    for (int o = 0; o < n_out; ++o) {
+        DMRG_REQUIRE(m[o] >= 0 && n[o] >= 0 && c_off[o] >= 0, DMRG_EINVAL, "bad block size");
+        ec = std::max<int64_t>(ec, c_off[o] + (int64_t)m[o] * n[o]);
+        std::vector<Seg> segs;
+        const int ns = seg_beg[o + 1] - seg_beg[o];
+        float tile_alpha = 1.0f;
+        for (int s = seg_beg[o]; s < seg_beg[o + 1]; ++s) {
+            DMRG_REQUIRE(k[s] >= 0 && lda[s] >= 1 && ldb[s] >= 1, DMRG_EINVAL, "bad segment");
+            DMRG_REQUIRE(lda[s] % 8 == 0 && ldb[s] % 8 == 0 && a_off[s] % 8 == 0 && b_off[s] % 8 == 0, DMRG_EINVAL,
+                         "tensor-core operands need 8-element aligned offsets and leading dimensions");
+            Seg g{};
+            g.a_off = a_off[s];
+            g.b_off = b_off[s];
+            g.k = k[s];
+            g.lda = lda[s];
+            g.ldb = ldb[s];
+            g.a_tr = (uint8_t)(a_tr[s] != 0);
+            g.b_tr = (uint8_t)(b_tr[s] != 0);
+            g.a_buf = 0;
+            g.b_buf = 1;
+            if (ns == 1) {
+                tile_alpha = (float)alpha[s];
+                g.alpha = 1.0;
+            } else {
+                DMRG_REQUIRE(alpha[s] == 1.0 || alpha[s] == -1.0, DMRG_EINVAL, "segment alpha must be +-1");
+                g.alpha = alpha[s];
+            }
+            // extents of the operands read
+            const int64_t ar = g.a_tr ? g.k : m[o], ac = g.a_tr ? m[o] : g.k;
+            const int64_t br = g.b_tr ? n[o] : g.k, bc = g.b_tr ? g.k : n[o];
+            if (ar > 0 && ac > 0) ea = std::max<int64_t>(ea, g.a_off + (ar - 1) * g.lda + ac);
+            if (br > 0 && bc > 0) eb = std::max<int64_t>(eb, g.b_off + (br - 1) * g.ldb + bc);
+            segs.push_back(g);
+        }
+        wl.add_block(c_off[o], 2, m[o], n[o], n[o], segs, TC_ATOMIC_F64, 0, 128, tile_alpha);
+    }
+    const int64_t ea_n = ea, eb_n = eb;  // elements actually present in a / b
+    ea = round_up(ea, 8);
+    eb = round_up(eb, 8);
+    __nv_bfloat16 *ha = nullptr, *la = nullptr, *hb = nullptr, *lb = nullptr;
+    int* ctr = nullptr;
+    DMRG_CHECK_CUDA(cudaMalloc(&ha, ea * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&la, ea * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&hb, eb * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&lb, eb * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&ctr, 2 * sizeof(int)));
+    DMRG_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st));
+    DMRG_REQUIRE(ea < 2147483647 && eb < 2147483647, DMRG_EINVAL, "operand too large");
+    dev_split_f64(a, 1, (int)ea_n, ea_n, ha, la, ea, st);
+    dev_split_f64(b, 1, (int)eb_n, eb_n, hb, lb, eb, st);
+    if (ec > 0) DMRG_CHECK_CUDA(cudaMemsetAsync(c, 0, ec * 8, st));
+    wl.upload(st);
+    TcBufs tb{};
+    tb.hi[0] = ha;
+    tb.lo[0] = la;
+    tb.hi[1] = hb;
+    tb.lo[1] = lb;
+    tb.out[2] = c;
+    tb.counter = ctr;
+    tb.err = ctr + 1;
+    launch_seg_gemm_tc(wl, tb, 1, nsplit, st);
+    int err = 0;
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(&err, ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    wl.release();
+    cudaFree(ha);
+    cudaFree(la);
+    cudaFree(hb);
+    cudaFree(lb);
+    cudaFree(ctr);
+    if (err) return fail(nullptr, DMRG_ETIMEOUT, "tensor-core kernel wait timed out");
+    return DMRG_OK;
 }
 
 cudaStream_t pick(dmrg_plan_t plan, void* stream) {
@@ -300,7 +387,16 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
                               const int64_t* b_off, const int* ldb, const int* b_tr, const double* alpha,
                               const double* a, const double* b, double* c, void* stream) {
     if (n_out < 0 || !m || !n || !c_off || !seg_beg || !a || !b || !c) return fail(nullptr, DMRG_EINVAL, "bad arguments");
-    if (precision != DMRG_FP64) return fail(nullptr, DMRG_EINVAL, "precision mode not available in this build");
+    if (precision != DMRG_FP64 && precision != DMRG_BF16X3 && precision != DMRG_BF16)
+        return fail(nullptr, DMRG_EINVAL, "unknown precision");
+    if (precision != DMRG_FP64) {
+        try {
+            return grouped_gemm_tc(precision == DMRG_BF16X3 ? 2 : 1, n_out, m, n, c_off, seg_beg, k, a_off, lda, a_tr,
+                                   b_off, ldb, b_tr, alpha, a, b, c, (cudaStream_t)stream);
+        } catch (const Error& e) {
+            return fail(nullptr, e.code, e.what());
+        }
+    }
     try {
         cudaStream_t st = (cudaStream_t)stream;
         WorkList wl;

@@ -30,6 +30,7 @@ struct Tile {
     int32_t m0, n0;       // tile origin inside the block
     int32_t seg_beg, seg_end;
     uint8_t c_buf, mode, pad0, pad1;
+    float alpha;          // epilogue scale (tensor-core engine; the FP64 engine scales per segment)
 };
 
 constexpr int kMaxBufs = 8;
@@ -56,7 +57,7 @@ struct WorkList {
     // Add an output block with its segments, split into 64x64 tiles (and into
     // K-chunks of at most kchunk when the block is atomically accumulated).
     void add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<Seg>& s,
-                   uint8_t mode, int64_t kchunk = 0);
+                   uint8_t mode, int64_t kchunk = 0, int tile = 64, float alpha = 1.0f);
     void upload(cudaStream_t st);
     void release();
 };

@@ -18,11 +18,12 @@ int64_t& launch_counter() {
 // ---------------------------------------------------------------------------
 
 void WorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<Seg>& s,
-                         uint8_t mode, int64_t kchunk) {
+                         uint8_t mode, int64_t kchunk, int tile, float alpha) {
     if (m <= 0 || n <= 0) return;
     // split segments into K-chunks (only for atomically accumulated blocks)
     std::vector<std::pair<int, int>> chunks;
-    if (mode == TILE_ATOMIC && kchunk > 0) {
+    const bool atomic = (mode == TILE_ATOMIC || mode == 2 || mode == 4);
+    if (atomic && kchunk > 0) {
         int beg = 0;
         int64_t acc = 0;
         for (int i = 0; i < (int)s.size(); ++i) {
@@ -44,9 +45,10 @@ void WorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const 
             flops += 2.0 * m * n * (double)s[i].k;
         }
         int se = (int)segs.size();
-        for (int m0 = 0; m0 < m; m0 += 64)
-            for (int n0 = 0; n0 < n; n0 += 64) {
+        for (int m0 = 0; m0 < m; m0 += tile)
+            for (int n0 = 0; n0 < n; n0 += tile) {
                 Tile t{};
+                t.alpha = alpha;
                 t.c_off = c_off;
                 t.ldc = ldc;
                 t.m = m;

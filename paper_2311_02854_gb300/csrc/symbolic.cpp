@@ -35,6 +35,7 @@ void layout_family(Family& f, const Basis& b) {
     f.ket.clear();
     f.bra.clear();
     f.off.clear();
+    f.ld.clear();
     int64_t off = 0;
     for (int i = 0; i < b.size(); ++i) {
         int j = b.find(b.qn[i] + f.dq);
@@ -43,7 +44,9 @@ void layout_family(Family& f, const Basis& b) {
         f.ket.push_back(i);
         f.bra.push_back(j);
         f.off.push_back(off);
-        off += (int64_t)b.dim[j] * b.dim[i];
+        const int ldi = (int)round_up(b.dim[i], 8);  // rows padded to 16 bytes of bf16
+        f.ld.push_back(ldi);
+        off += (int64_t)b.dim[j] * ldi;
     }
     f.nnz = off;
     f.stride = round_up(std::max<int64_t>(off, 1), 32);

@@ -40,6 +40,7 @@ struct Family {
     std::vector<int> pair_of_ket;  // ket sector -> pair index, -1 if none
     std::vector<int> ket, bra;     // per pair
     std::vector<int64_t> off;      // per pair, element offset inside an op
+    std::vector<int> ld;           // per pair, row pitch (ket dim rounded up to 8)
     int64_t nnz = 0, stride = 0;
     int64_t base = 0;              // element offset of row 0 in the owning buffer
     int nops() const { return (int)keys.size(); }
