@@ -1,0 +1,368 @@
+"""Benchmark of the two-site DMRG hot path (sigma = H psi, Davidson, decimation,
+renormalisation) on seeded synthetic inputs shaped like the K=73 / N=114
+active space, at bond dimension D=3000.
+
+One step = two bond updates at the middle of the chain: Davidson at bond
+(k, k+1) with the mixed-precision sigma, decimation to D with renormalisation
+of the grown left block, Davidson at (k+1, k+2), decimation back.  Reported
+value: algorithmic TFLOP/s of the step (sigma + renormalisation + intermediate
+products / device time of the step); sigma alone, seconds per site and the
+end-to-end rate (host buffers, copies in the timed region) ride along.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic_inputs as si  # noqa: E402
+
+WORKLOADS = {
+    # name: K, N, 2Sz, D, n_chol, ell, h_min, Gaussian sector widths
+    "k73_d3000": dict(K=73, N=114, twoS=0, D=3000, n_chol=292, ell=8.0, h_min=-6.0, wn=1.45, ws=1.45),
+    "k36_d1000": dict(K=36, N=36, twoS=0, D=1000, n_chol=144, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
+    "k24_d500": dict(K=24, N=24, twoS=0, D=500, n_chol=96, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
+}
+METRIC = "sigma=H*psi TFLOP/s, s/site at K=73,D=3000; mixed vs FP64 at dE<=1e-6 Eh"
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2}
+# bounded sample the CPU oracle runs for the baseline (same recipe, small K)
+CPU_SAMPLE = dict(K=14, N=14, twoS=0, D=600, n_chol=56, ell=3.0, h_min=-4.0, wn=1.0, ws=1.0)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(w, tmpdir, center):
+    h, L = si.make_integrals(w["K"], w["n_chol"], ell=w["ell"], h_min=w["h_min"], seed=0)
+    bonds = si.bond_sectors(w["K"], w["N"], w["twoS"], w["D"], split="gaussian", width_n=w["wn"], width_s=w["ws"])
+    mps = si.random_mps(w["K"], w["N"], w["twoS"], bonds, center=center, seed=2)
+    path = os.path.join(tmpdir, "mps.bin")
+    si.write_mps(path, mps)
+    return h, L, bonds, path
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        load = [s for s in sm if s > 0]
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same recipe)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(n_sigma=3, flops=None):
+    """Time the CPU oracle's sigma on the bounded sample; returns (TFLOP/s, seconds, cores)."""
+    from oracle.dmrg import Oracle
+    from oracle.hamiltonian import eri_from_cholesky
+    w = CPU_SAMPLE
+    k = w["K"] // 2
+    h, L = si.make_integrals(w["K"], w["n_chol"], ell=w["ell"], h_min=w["h_min"], seed=0)
+    bonds = si.bond_sectors(w["K"], w["N"], w["twoS"], w["D"], split="gaussian", width_n=w["wn"], width_s=w["ws"])
+    mps = si.random_mps(w["K"], w["N"], w["twoS"], bonds, center=k, seed=2)
+    ts = Oracle(h, eri_from_cholesky(L), w["N"], w["twoS"], mps).two_site(k)
+    psi = si.random_vector(ts.dim, seed=1)
+    ts.sigma(psi)  # builds the term list once
+    t0 = time.perf_counter()
+    for _ in range(n_sigma):
+        ts.sigma(psi)
+    dt = (time.perf_counter() - t0) / n_sigma
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    return (flops / dt / 1e12 if flops else None), dt, cores
+
+
+def sample_flops():
+    """Algorithmic sigma FLOPs of the bounded sample (the library's planner count)."""
+    import paper_2311_02854_gb300 as g
+    w = CPU_SAMPLE
+    k = w["K"] // 2
+    with tempfile.TemporaryDirectory() as td:
+        h, L, bonds, path = make_inputs(w, td, k)
+        plan = g.Plan(h, L, w["K"], w["N"], w["twoS"], w["D"], path, precision=0)
+        plan.set_bond(k)
+        f = plan.stats()["sigma_flops"]
+        plan.close()
+    return f
+
+
+# ---------------------------------------------------------------------------
+# own arm
+# ---------------------------------------------------------------------------
+
+def run_mine(args):
+    import torch
+    import paper_2311_02854_gb300 as g
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    w = WORKLOADS[args.workload]
+    K, D = w["K"], w["D"]
+    k = K // 2
+    prec = PRECISIONS[args.precision]
+    t_setup = time.time()
+    td = tempfile.mkdtemp(prefix="dmrg_bench_")
+    h, L, bonds, path = make_inputs(w, td, k)
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=prec, tol=args.tol, max_iter=args.dav_iters,
+                  keep_envs=0)
+    stream = torch.cuda.Stream()
+    plan.set_bond(k, stream=stream)
+    dim = plan.dim
+    psi = torch.from_numpy(si.random_vector(dim, seed=1)).cuda()
+    setup_s = time.time() - t_setup
+    st0 = plan.stats()
+
+    def bond_update(x, forward):
+        e, it, conv = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters, stream=stream)
+        cap = 4 * max(x.numel(), 1) + 64
+        nxt = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        wdisc, nd = plan.decimate(x, 1, D, forward, next_psi=nxt, next_cap=cap, stream=stream)
+        return nxt[:nd].clone(), e[0], it, wdisc
+
+    def step(x):
+        x, e1, it1, w1 = bond_update(x, True)
+        x, e2, it2, w2 = bond_update(x, False)
+        return x, (e1, e2), it1 + it2
+
+    def flops_now():
+        s = plan.stats()
+        return s
+
+    # warm-up
+    x = psi
+    for _ in range(args.warmup):
+        x, _, _ = step(x)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    s_before = plan.stats()
+    clock = ClockSampler(local)
+    clock.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    energies, iters = [], 0
+    for _ in range(args.steps):
+        x, e, it = step(x)
+        energies.append(e)
+        iters += it
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clock.stop()
+    ms = ev0.elapsed_time(ev1)
+    s_after = plan.stats()
+    # sigma-only rate: one timed sigma call per vector size
+    y = torch.empty_like(x)
+    sig_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.sigma(x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sig_ms.append(e0.elapsed_time(e1))
+    s_sig = plan.stats()
+    sigma_flops = s_sig["sigma_flops"]
+    n_sig = s_after["sigma_calls"] - s_before["sigma_calls"]
+    # algorithmic FLOPs of the timed steps: sigma calls at the two bonds (both
+    # middle bonds have the same planned count to within a few percent; the
+    # count of the bond current at the end is used) plus renormalisations
+    renorm_fl = s_after["renorm_flops_last"]
+    step_flops = n_sig * sigma_flops + 2 * args.steps * (renorm_fl + s_after["interm_flops"])
+    max_ms = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        max_ms = float(t.item())
+    value = world * step_flops / (max_ms / 1e3) / 1e12
+    sig_t = statistics.median(sig_ms)
+    sigma_tflops = sigma_flops / (sig_t / 1e3) / 1e12
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    # end-to-end: the same step with the guess from pinned host memory and the
+    # final vector read back every step
+    host_in = torch.from_numpy(x.cpu().numpy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    t0 = time.perf_counter()
+    xe = None
+    for _ in range(max(1, args.e2e_steps)):
+        xe = host_in.to("cuda", non_blocking=True)
+        xe, _, _ = step(xe)
+        host_out = xe.to("cpu")
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+    e2e_value = world * (step_flops / args.steps) / e2e_s / 1e12
+    st_end = plan.stats()
+    launches = s_after["kernel_launches"] - s_before["kernel_launches"]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"{args.workload}: K={K}, N={w['N']}, 2Sz={w['twoS']}, D={D}, n_chol={w['n_chol']}, "
+                               f"middle bond {k}, Gaussian sector split (widths {w['wn']}), seeded",
+                   "global_batch": world, "seq_len": D, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (operator store ~%.1f GB)" % (st_end["store_bytes"] / 1e9),
+                   "step": "2 bond updates (Davidson <= %d it, decimation, renormalisation)" % args.dav_iters},
+        "s_per_site": round(max_ms / 1e3 / (2 * args.steps), 4),
+        "sigma_tflops": round(sigma_tflops, 3),
+        "sigma_ms": round(sig_t, 3),
+        "sigma_flops": sigma_flops,
+        "davidson_iters_per_step": iters / args.steps,
+        "energies": [list(map(float, e)) for e in energies],
+        "setup_s": round(setup_s, 1),
+        "host_plan_ms_total": round(st_end["ms_host_plan"], 1),
+        "renorm_ms_total": round(st_end["ms_renorm"], 1),
+        "davidson_ms_total": round(st_end["ms_davidson"], 1),
+        "decim_ms_total": round(st_end["ms_decim"], 1),
+        "sigma_terms": st_end["n_terms"], "sigma_items": st_end["n_items"],
+        "roofline": {"bound": "tensor", "achieved": round(sigma_tflops, 3), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(sigma_tflops / peak, 4), "traffic": None,
+                     "peak_source": f"{src} bf16 sustained", "kernel": "tc_seg_gemm_kernel (sigma call)"},
+        "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": int(dim * 8),
+                "d2h_bytes_per_step": int(dim * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "device_bytes": st_end["device_bytes"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        f = sample_flops()
+        rate, dt, cores = oracle_sample_rate(3, f)
+        out["cpu_baseline"] = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": f"oracle sigma at K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']} middle bond "
+                                         f"(same recipe), {dt:.2f} s per sigma, FLOPs by the planner count"}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    f = None
+    try:
+        f = sample_flops()
+    except Exception:
+        f = None
+    for _ in range(args.warmup):
+        oracle_sample_rate(1, f)
+    rates, dts = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, dt, cores = oracle_sample_rate(1, f)
+        rates.append(r if r is not None else 0.0)
+        dts.append(dt)
+    total = time.perf_counter() - t0
+    value = statistics.median(rates) if rates else None
+    w = WORKLOADS[args.workload]
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: K={w['K']}, D={w['D']} (oracle on a bounded sample "
+                                  f"K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']})"},
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                            "sample": f"oracle sigma at K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']} per step"},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="k73_d3000", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
+    ap.add_argument("--dav-iters", type=int, default=8)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

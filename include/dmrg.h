@@ -77,8 +77,9 @@ typedef struct {
     int max_iter;           /* Davidson iterations per bond */
     int max_space;          /* Davidson subspace size (0 => 20 * n_roots) */
     int precond;            /* dmrg_precond */
-    int fp64_final;         /* 1: mixed modes end each Davidson with one FP64 sigma
-                               and an FP64 Rayleigh quotient */
+    int fp64_final;         /* 1: mixed modes report FP64 Rayleigh quotients <x|H|x>
+                               (one FP64-arithmetic sigma per root after Davidson);
+                               default 0 */
     int64_t mem_budget;     /* device bytes the plan may hold (0 => 90% of free) */
     int64_t scratch_bytes;  /* sigma GEMM scratch per chunk (0 => automatic) */
     int keep_envs;          /* 1: keep every bond's environment (sweeps) */
@@ -100,6 +101,7 @@ typedef struct {
     int64_t kernel_launches;      /* kernels launched by the library since the plan was made */
     int64_t precond_fallbacks;    /* MLP -> Jacobi fallbacks */
     int davidson_iters_last;
+    double ms_host_plan;          /* host time spent building work lists (all calls) */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */
@@ -141,6 +143,13 @@ dmrg_status dmrg_layout(dmrg_plan_t plan, int64_t* dim, int* n_sectors, int64_t*
 dmrg_status dmrg_sigma(dmrg_plan_t plan, const double* psi_dev, double* sigma_dev, int nvec,
                        void* stream);
 
+/* sigma = H psi evaluated in FP64 arithmetic over the plan's stored operators
+ * (in the mixed modes the bf16 pieces are upcast exactly, hi + lo), on the
+ * FP64 engine.  Separates the error of the mixed-precision products from the
+ * rounding of the stored operators.  Same buffers as dmrg_sigma. */
+dmrg_status dmrg_sigma_fp64(dmrg_plan_t plan, const double* psi_dev, double* sigma_dev, int nvec,
+                            void* stream);
+
 /* Same as dmrg_sigma with HOST buffers (copies to and from the device inside;
  * the end-to-end path of the benchmark). */
 dmrg_status dmrg_sigma_host(dmrg_plan_t plan, const double* psi_host, double* sigma_host,
@@ -160,11 +169,15 @@ dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi_dev, int n_roots, double
                           int precond, double* energies, int* iters, void* stream);
 
 /* Decimation (Sec. 2.1): truncate the current bond's two-site vectors psi_dev
- * (n_roots of them; state-averaged density matrix if > 1) to at most D states,
- * update A[k] (forward) or A[k+1] (backward), renormalise the grown block and
- * move to the next bond.  next_psi_dev (may be NULL) receives the guess for the
- * next bond (its length is dmrg_layout of the new bond times n_roots; query the
- * size with next_dim). */
+ * (n_roots of them; state-averaged density matrix if > 1) to at most D states
+ * (largest density-matrix eigenvalues, ties by sector order then rank), update
+ * A[k] (forward) or A[k+1] (backward), renormalise the grown block and make the
+ * next bond (k+1 or k-1) current.
+ *  discarded     out: sum of the dropped eigenvalues.
+ *  next_dim      in: capacity of next_psi_dev in elements per root (0 if
+ *                next_psi_dev is NULL); out: length of the next bond's vector.
+ *  next_psi_dev  receives the guess for the next bond (U^T psi A[k+2] or
+ *                A[k-1] psi V) when the capacity suffices. */
 dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi_dev, int n_roots, int D, int forward,
                           double* discarded, double* next_psi_dev, int64_t* next_dim, void* stream);
 

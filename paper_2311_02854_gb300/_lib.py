@@ -35,7 +35,8 @@ class Stats(C.Structure):
                 ("ms_davidson", C.c_double), ("ms_decim", C.c_double), ("ms_hdiag", C.c_double),
                 ("n_terms", C.c_int64), ("n_items", C.c_int64), ("store_bytes", C.c_int64),
                 ("interm_bytes", C.c_int64), ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
-                ("precond_fallbacks", C.c_int64), ("davidson_iters_last", C.c_int)]
+                ("precond_fallbacks", C.c_int64), ("davidson_iters_last", C.c_int),
+                ("ms_host_plan", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -59,6 +60,7 @@ _SIGS = {
     "dmrg_layout": (C.c_int, [_P, _L, _I, _L, _I]),
     "dmrg_sigma": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dmrg_sigma_host": (C.c_int, [_P, _D, _D, C.c_int, _P]),
+    "dmrg_sigma_fp64": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dmrg_hdiag": (C.c_int, [_P, _P, _P]),
     "dmrg_davidson": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _D, _I, _P]),
     "dmrg_decimate": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _D, _P, _L, _P]),
@@ -185,6 +187,9 @@ class Plan:
 
     def sigma(self, psi, out, nvec=1, stream=None):
         self._call("dmrg_sigma", _ptr(psi), _ptr(out), int(nvec), _stream(stream))
+
+    def sigma_fp64(self, psi, out, nvec=1, stream=None):
+        self._call("dmrg_sigma_fp64", _ptr(psi), _ptr(out), int(nvec), _stream(stream))
 
     def sigma_host(self, psi, out, nvec=1, stream=None):
         assert psi.dtype == np.float64 and out.dtype == np.float64

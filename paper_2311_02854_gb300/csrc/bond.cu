@@ -1,8 +1,10 @@
 // Environments and the current bond: vacuum blocks, renormalisation
 // (Eq. Renorm / Eqs. renorm12-renormFinal), the bond's intermediates (the
 // "intermediates" step of Sec. 2.2) and the sigma / diag(H_eff) work lists
-// (Eqs. sigmablk56-sigmablk).
+// (Eqs. sigmablk56-sigmablk).  Two engines share the planning: FP64 (SIMT
+// kernel, 64x64 tiles) and the tcgen05 engine on bf16 pieces (mixed precision).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 
 #include "bond.h"
@@ -11,20 +13,21 @@ namespace dmrg {
 
 namespace {
 
-// Buffer ids of the BufTable used by every work list.
+// Buffer ids of the tables used by every work list.
 enum : int8_t { BUF_L = 0, BUF_R = 1, BUF_INT = 2, BUF_PSI = 3, BUF_SCR = 4, BUF_ID = 5, BUF_OUT = 6, BUF_W = 7 };
+
+constexpr int64_t kChunkF64 = 1 << 14;  // K-depth per accumulation pass (FP64 engine)
+constexpr int64_t kChunkTC = 1 << 15;   // K-depth per accumulation pass (tensor cores)
 
 struct OpLookup {
     bool ok = false;
-    int j = -1;   // bra sector
-    View v;       // view of the effective operator block (d_j x d_i)
+    int j = -1;  // bra sector
+    View v;      // view of the effective operator block (d_j x d_i)
 };
-
-}  // namespace
 
 // Lookup of an operator reference acting on ket sector i of `lay`.
 // Stored rows live in buffer `store_buf`, intermediates in BUF_INT.
-static OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r, int i, int8_t store_buf) {
+OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r, int i, int8_t store_buf) {
     OpLookup o;
     if (r.src == SRC_I) {
         o.ok = true;
@@ -69,78 +72,88 @@ static OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r
     return o;
 }
 
-static int ref_parity(const BlockLayout& lay, const Interms& im, const OpRef& r) {
+int ref_parity(const BlockLayout& lay, const Interms& im, const OpRef& r) {
     if (r.src == SRC_I) return 0;
     if (r.src == SRC_STORE) return kind_parity(lay.fams[r.fam].kind);
     return kind_parity(lay.fams[im.fams[r.fam].src_fam].kind);
 }
 
-// ---------------------------------------------------------------------------
-// Intermediates: Int[rows x nnz] = W[rows x nops] * Family[nops x nnz]
-// ---------------------------------------------------------------------------
-
-void form_interms(Plan& P, Interms& im, const Block* blocks[2], double*& d_int, int64_t& n_int,
-                  double& flops) {
-    int64_t total = 0, wtot = 0;
-    for (auto& IF : im.fams) {
-        const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
-        IF.base = total;
-        total += (int64_t)IF.rows.size() * f.stride;
-        wtot += (int64_t)IF.rows.size() * f.nops();
-    }
-    P.free(d_int, n_int);
-    n_int = total;
-    d_int = P.alloc(std::max<int64_t>(total, 1));
-    flops = 0.0;
-    if (im.fams.empty()) return;
-    std::vector<double> W(wtot, 0.0);
-    WorkList wl;
-    int64_t woff = 0;
-    for (auto& IF : im.fams) {
-        const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
-        const int nr = (int)IF.rows.size(), no = f.nops();
-        for (int r = 0; r < nr; ++r)
-            for (auto& rc : IF.rows[r]) W[woff + (int64_t)r * no + rc.first] += rc.second;
-        Seg s{};
-        s.a_off = woff;
-        s.b_off = f.base;
-        s.k = no;
-        s.lda = no;
-        s.ldb = (int)f.stride;
-        DMRG_REQUIRE(f.stride < (1LL << 31), DMRG_EINVAL, "operator family too large");
-        s.a_buf = BUF_W;
-        s.b_buf = (uint8_t)IF.owner;  // BUF_L or BUF_R
-        s.alpha = 1.0;
-        wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TILE_STORE);
-        woff += (int64_t)nr * no;
-    }
-    flops = wl.flops;
-    if (wtot > P.n_wcoef) {
-        P.free(P.d_wcoef, P.n_wcoef);
-        P.n_wcoef = wtot;
-        P.d_wcoef = P.alloc(wtot);
-    }
-    DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_wcoef, W.data(), wtot * 8, cudaMemcpyHostToDevice, P.stream));
-    wl.upload(P.stream);
-    BufTable bt{};
-    bt.p[BUF_L] = blocks[0] ? blocks[0]->d : nullptr;
-    bt.p[BUF_R] = blocks[1] ? blocks[1]->d : nullptr;
-    bt.p[BUF_INT] = d_int;
-    bt.p[BUF_W] = P.d_wcoef;
-    launch_seg_gemm_f64(wl, bt, 1, P.stream);
-    DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
-    wl.release();
+double host_ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+float* alloc_f32(Plan& P, int64_t n) { return (float*)P.alloc_bf16(2 * n); }
+void free_f32(Plan& P, float*& p, int64_t n) {
+    __nv_bfloat16* q = (__nv_bfloat16*)p;
+    P.free_bf16(q, 2 * n);
+    p = nullptr;
+}
+
+void ensure_counter(Plan& P) {
+    if (!P.d_ctr) {
+        DMRG_CHECK_CUDA(cudaMalloc(&P.d_ctr, 2 * sizeof(int)));
+        DMRG_CHECK_CUDA(cudaMemset(P.d_ctr, 0, 2 * sizeof(int)));
+    }
+}
+
+TcBufs tc_base(Plan& P) {
+    ensure_counter(P);
+    TcBufs tb{};
+    tb.counter = P.d_ctr;
+    tb.err = P.d_ctr + 1;
+    return tb;
+}
+
+}  // namespace
+
+void free_block(Plan& P, std::unique_ptr<Block>& b) {
+    if (!b) return;
+    P.free(b->d, b->n);
+    P.free_bf16(b->h, b->n);
+    P.free_bf16(b->l, b->n);
+    b.reset();
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
 void ensure_ident(Plan& P, int n) {
-    if (n <= P.ident_n) return;
-    P.free(P.d_ident, (int64_t)P.ident_n * P.ident_n);
-    P.ident_n = std::max(n, 64);
-    P.d_ident = P.alloc((int64_t)P.ident_n * P.ident_n);
-    dev_identity(P.d_ident, P.ident_n, P.stream);
+    n = (int)round_up(std::max(n, 64), 8);
+    if (n > P.ident_n) {
+        P.free(P.d_ident, (int64_t)P.ident_n * P.ident_n);
+        P.ident_n = n;
+        P.d_ident = P.alloc((int64_t)n * n);
+        dev_identity(P.d_ident, n, P.stream);
+    }
+    if (P.mixed() && P.id_n != P.ident_n) {
+        P.free_bf16(P.id_hi, (int64_t)P.id_n * P.id_n);
+        P.free_bf16(P.id_lo, (int64_t)P.id_n * P.id_n);
+        P.id_n = P.ident_n;
+        const int64_t nn = (int64_t)P.id_n * P.id_n;
+        P.id_hi = P.alloc_bf16(nn);
+        P.id_lo = P.alloc_bf16(nn);
+        dev_split_f64(P.d_ident, 1, (int)nn, nn, P.id_hi, P.id_lo, nn, P.stream);
+    }
 }
 
 void ensure_scratch(Plan& P, int64_t n) {
+    if (P.mixed()) {
+        if (n <= P.n_spc) return;
+        P.free_bf16(P.s_hi, P.n_spc);
+        P.free_bf16(P.s_lo, P.n_spc);
+        P.n_spc = n;
+        P.s_hi = P.alloc_bf16(n);
+        P.s_lo = P.alloc_bf16(n);
+        return;
+    }
+    if (n <= P.n_scratch) return;
+    P.free(P.d_scratch, P.n_scratch);
+    P.n_scratch = n;
+    P.d_scratch = P.alloc(n);
+}
+
+void ensure_scratch_f64(Plan& P, int64_t n) {
     if (n <= P.n_scratch) return;
     P.free(P.d_scratch, P.n_scratch);
     P.n_scratch = n;
@@ -148,9 +161,106 @@ void ensure_scratch(Plan& P, int64_t n) {
 }
 
 int64_t scratch_cap(const Plan& P) {
-    int64_t cap = P.opt.scratch_bytes > 0 ? P.opt.scratch_bytes / 8 : 0;
-    if (cap <= 0) cap = std::max<int64_t>((int64_t)1 << 26, P.budget / 8 / 16);  // >= 512 MiB
+    const int64_t esz = P.mixed() ? 4 : 8;  // two bf16 pieces or one double per element
+    int64_t cap = P.opt.scratch_bytes > 0 ? P.opt.scratch_bytes / esz : 0;
+    if (cap <= 0) cap = std::max<int64_t>((int64_t)1 << 27, P.budget / esz / 12);
     return cap;
+}
+
+// ---------------------------------------------------------------------------
+// Intermediates: Int[rows x nnz] = W[rows x nops] * Family[nops x nnz]
+// ---------------------------------------------------------------------------
+
+void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops) {
+    int64_t total = 0, wtot = 0;
+    for (auto& IF : im.fams) {
+        const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
+        IF.base = total;
+        total += (int64_t)IF.rows.size() * f.stride;
+        wtot += (int64_t)IF.rows.size() * round_up(f.nops(), 8);
+    }
+    free_interms(P, S);
+    S.n = std::max<int64_t>(total, 32);
+    flops = 0.0;
+    if (P.mixed()) {
+        S.h = P.alloc_bf16(S.n);
+        S.l = P.alloc_bf16(S.n);
+    } else {
+        S.d = P.alloc(S.n);
+    }
+    if (im.fams.empty()) return;
+    std::vector<double> W(std::max<int64_t>(wtot, 8), 0.0);
+    WorkList wl;
+    int64_t woff = 0;
+    for (auto& IF : im.fams) {
+        const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
+        const int nr = (int)IF.rows.size(), no = f.nops();
+        const int ldw = P.mixed() ? (int)round_up(no, 8) : no;
+        for (int r = 0; r < nr; ++r)
+            for (auto& rc : IF.rows[r]) W[woff + (int64_t)r * ldw + rc.first] += rc.second;
+        DMRG_REQUIRE(f.stride < (1LL << 31), DMRG_EINVAL, "operator family too large");
+        Seg s{};
+        s.a_off = woff;
+        s.b_off = f.base;
+        s.k = no;
+        s.lda = ldw;
+        s.ldb = (int)f.stride;
+        s.a_buf = BUF_W;
+        s.b_buf = (uint8_t)IF.owner;  // BUF_L or BUF_R
+        s.alpha = 1.0;
+        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_STORE_SPLIT, 0, 128, 1.0f);
+        else wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TILE_STORE);
+        woff += (int64_t)nr * ldw;
+    }
+    flops = wl.flops;
+    const int64_t wn = (int64_t)W.size();
+    if (wn > P.n_wcoef) {
+        P.free(P.d_wcoef, P.n_wcoef);
+        P.n_wcoef = wn;
+        P.d_wcoef = P.alloc(wn);
+    }
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_wcoef, W.data(), wn * 8, cudaMemcpyHostToDevice, P.stream));
+    wl.upload(P.stream);
+    if (P.mixed()) {
+        if (wn > P.n_wpc) {
+            P.free_bf16(P.w_hi, P.n_wpc);
+            P.free_bf16(P.w_lo, P.n_wpc);
+            P.n_wpc = wn;
+            P.w_hi = P.alloc_bf16(wn);
+            P.w_lo = P.alloc_bf16(wn);
+        }
+        dev_split_f64(P.d_wcoef, 1, (int)wn, wn, P.w_hi, P.w_lo, wn, P.stream);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(S.h, 0, S.n * 2, P.stream));
+        DMRG_CHECK_CUDA(cudaMemsetAsync(S.l, 0, S.n * 2, P.stream));
+        TcBufs tb = tc_base(P);
+        for (int o = 0; o < 2; ++o)
+            if (blocks[o]) {
+                tb.hi[o] = blocks[o]->h;
+                tb.lo[o] = blocks[o]->l;
+            }
+        tb.hi[BUF_W] = P.w_hi;
+        tb.lo[BUF_W] = P.w_lo;
+        tb.out[BUF_INT] = S.h;
+        tb.out_lo[BUF_INT] = S.l;
+        launch_seg_gemm_tc(wl, tb, 1, P.nsplit, P.stream);
+        P.check_device_error();
+    } else {
+        BufTable bt{};
+        bt.p[BUF_L] = blocks[0] ? blocks[0]->d : nullptr;
+        bt.p[BUF_R] = blocks[1] ? blocks[1]->d : nullptr;
+        bt.p[BUF_INT] = S.d;
+        bt.p[BUF_W] = P.d_wcoef;
+        launch_seg_gemm_f64(wl, bt, 1, P.stream);
+    }
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+    wl.release();
+}
+
+void free_interms(Plan& P, IntermStore& S) {
+    P.free(S.d, S.n);
+    P.free_bf16(S.h, S.n);
+    P.free_bf16(S.l, S.n);
+    S.n = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -163,9 +273,16 @@ std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end) {
     b.add(QN(0, 0), 1);
     int lo = right_end ? P.n_so : 0;
     B->lay.build(b, lo, lo, P.n_so);
-    B->n = std::max<int64_t>(B->lay.total, 1);
-    B->d = P.alloc(B->n);
-    dev_fill(B->d, 0.0, B->n, P.stream);
+    B->n = std::max<int64_t>(B->lay.total, 32);
+    if (P.mixed()) {
+        B->h = P.alloc_bf16(B->n);
+        B->l = P.alloc_bf16(B->n);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(B->h, 0, B->n * 2, P.stream));
+        DMRG_CHECK_CUDA(cudaMemsetAsync(B->l, 0, B->n * 2, P.stream));
+    } else {
+        B->d = P.alloc(B->n);
+        dev_fill(B->d, 0.0, B->n, P.stream);
+    }
     return B;
 }
 
@@ -178,28 +295,49 @@ Basis bond_basis(const Plan& P, int b, bool right_side) {
     return bs;
 }
 
-// Packed device copy of site tensor A[k]; key -> (offset, d_l, d_r)
+// Device copy of site tensor A[k] with rows padded to 8: key -> (offset, ld).
 struct SiteDev {
     double* d = nullptr;
+    __nv_bfloat16 *h = nullptr, *l = nullptr;
     int64_t n = 0;
-    std::map<std::array<int, 3>, int64_t> off;
+    std::map<std::array<int, 3>, std::pair<int64_t, int>> off;
 };
 
 static SiteDev upload_site(Plan& P, int k) {
     SiteDev S;
     int64_t tot = 0;
+    const auto& bl = P.mps.bonds[k - 1];
+    const auto& br = P.mps.bonds[k];
     for (auto& kv : P.mps.sites[k]) {
-        S.off[kv.first] = tot;
-        tot += (int64_t)kv.second.size();
+        const int dl = bl[kv.first[0]][2], dr = br[kv.first[2]][2];
+        const int ld = (int)round_up(dr, 8);
+        S.off[kv.first] = {tot, ld};
+        tot += (int64_t)dl * ld;
     }
-    S.n = std::max<int64_t>(tot, 1);
-    S.d = P.alloc(S.n);
+    S.n = std::max<int64_t>(tot, 8);
     std::vector<double> host(S.n, 0.0);
-    for (auto& kv : P.mps.sites[k])
-        std::copy(kv.second.begin(), kv.second.end(), host.begin() + S.off[kv.first]);
+    for (auto& kv : P.mps.sites[k]) {
+        const int dl = bl[kv.first[0]][2], dr = br[kv.first[2]][2];
+        const auto o = S.off[kv.first];
+        for (int a = 0; a < dl; ++a)
+            std::copy(kv.second.begin() + (int64_t)a * dr, kv.second.begin() + (int64_t)(a + 1) * dr,
+                      host.begin() + o.first + (int64_t)a * o.second);
+    }
+    S.d = P.alloc(S.n);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(S.d, host.data(), S.n * 8, cudaMemcpyHostToDevice, P.stream));
+    if (P.mixed()) {
+        S.h = P.alloc_bf16(S.n);
+        S.l = P.alloc_bf16(S.n);
+        dev_split_f64(S.d, 1, (int)S.n, S.n, S.h, S.l, S.n, P.stream);
+    }
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     return S;
+}
+
+static void free_site(Plan& P, SiteDev& S) {
+    P.free(S.d, S.n);
+    P.free_bf16(S.h, S.n);
+    P.free_bf16(S.l, S.n);
 }
 
 // Grow block X by site m (forward: X = sites 1..m-1 -> sites 1..m) or
@@ -219,22 +357,24 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     build_renorm_terms(P.I, XL, OL, k0, forward, rp);
     // intermediates on X
     const Block* blocks[2] = {&X, nullptr};
-    double* d_int = nullptr;
-    int64_t n_int = 0;
+    IntermStore IS;
     double fl_int = 0.0;
-    form_interms(P, rp.interms, blocks, d_int, n_int, fl_int);
+    form_interms(P, rp.interms, blocks, IS, fl_int);
     SiteDev A = upload_site(P, m);
-    out->n = std::max<int64_t>(OL.total, 1);
-    out->d = P.alloc(out->n);
-    DMRG_CHECK_CUDA(cudaMemsetAsync(out->d, 0, out->n * 8, P.stream));
+    out->n = std::max<int64_t>(OL.total, 32);
 
+    const auto host0 = std::chrono::steady_clock::now();
     ProductList pl;
     std::map<std::pair<int, int>, int> outidx;  // (target, pair) -> out block
-    auto site_key = [&](int il, int n, int ir) {
+    auto site_view = [&](int il, int n, int ir, bool tr) {
+        View v;
         auto it = A.off.find({il, n, ir});
-        return it == A.off.end() ? (int64_t)-1 : it->second;
+        v.buf = BUF_PSI;
+        v.off = it->second.first;
+        v.ld = it->second.second;
+        v.tr = tr;
+        return v;
     };
-    // index A blocks by ket component
     std::vector<std::array<int, 3>> keys;
     for (auto& kv : P.mps.sites[m]) keys.push_back(kv.first);
     const auto& bl = P.mps.bonds[m - 1];
@@ -261,15 +401,15 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                     if (!ox.ok) continue;
                     const int jl = ox.j;
                     for (int c2 = 0; c2 < 4; ++c2) {
-                        double mv = M.at(c2, n);
+                        const double mv = M.at(c2, n);
                         if (mv == 0.0) continue;
                         auto bj = fwd_bra.find({jl, c2});
                         if (bj == fwd_bra.end()) continue;
                         const int jr = bj->second;
-                        int pr = of.pair_of_ket[ir];
+                        const int pr = of.pair_of_ket[ir];
                         if (pr < 0 || of.bra[pr] != jr) continue;
                         const int dl = bl[il][2], djl = bl[jl][2], dr = br[ir][2], djr = br[jr][2];
-                        double zeta = (M.parity && (XL.basis.qn[il].n & 1)) ? -1.0 : 1.0;
+                        const double zeta = (M.parity && (XL.basis.qn[il].n & 1)) ? -1.0 : 1.0;
                         auto key = std::make_pair(t, pr);
                         auto oi = outidx.find(key);
                         int o;
@@ -282,14 +422,9 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                         }
                         Contrib c;
                         c.out = o;
-                        c.P.buf = BUF_PSI;
-                        c.P.off = site_key(jl, c2, jr);
-                        c.P.ld = djr;
-                        c.P.tr = true;  // A(jl,c2,jr)^T : djr x djl
-                        c.Q = ox.v;     // X_eff : djl x dl
-                        c.R.buf = BUF_PSI;
-                        c.R.off = site_key(il, n, ir);
-                        c.R.ld = dr;    // A(il,n,ir) : dl x dr
+                        c.P = site_view(jl, c2, jr, true);  // A(jl,c2,jr)^T : djr x djl
+                        c.Q = ox.v;                          // X_eff : djl x dl
+                        c.R = site_view(il, n, ir, false);   // A(il,n,ir) : dl x dr
                         c.m = djr;
                         c.k1 = djl;
                         c.k2 = dl;
@@ -303,15 +438,15 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                     if (!ox.ok) continue;
                     const int jr = ox.j;
                     for (int n2 = 0; n2 < 4; ++n2) {
-                        double mv = M.at(n2, n);
+                        const double mv = M.at(n2, n);
                         if (mv == 0.0) continue;
                         auto bj = bwd_bra.find({n2, jr});
                         if (bj == bwd_bra.end()) continue;
                         const int jl = bj->second;
-                        int pr = of.pair_of_ket[il];
+                        const int pr = of.pair_of_ket[il];
                         if (pr < 0 || of.bra[pr] != jl) continue;
                         const int dl = bl[il][2], djl = bl[jl][2], dr = br[ir][2], djr = br[jr][2];
-                        double zeta = (parX && (kSiteQN[n].n & 1)) ? -1.0 : 1.0;
+                        const double zeta = (parX && (kSiteQN[n].n & 1)) ? -1.0 : 1.0;
                         auto key = std::make_pair(t, pr);
                         auto oi = outidx.find(key);
                         int o;
@@ -324,14 +459,9 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                         }
                         Contrib c;
                         c.out = o;
-                        c.P.buf = BUF_PSI;
-                        c.P.off = site_key(jl, n2, jr);
-                        c.P.ld = djr;   // A(jl,n2,jr) : djl x djr
-                        c.Q = ox.v;     // X_eff : djr x dr
-                        c.R.buf = BUF_PSI;
-                        c.R.off = site_key(il, n, ir);
-                        c.R.ld = dr;
-                        c.R.tr = true;  // A(il,n,ir)^T : dr x dl
+                        c.P = site_view(jl, n2, jr, false);  // A(jl,n2,jr) : djl x djr
+                        c.Q = ox.v;                           // X_eff : djr x dr
+                        c.R = site_view(il, n, ir, true);     // A(il,n,ir)^T : dr x dl
                         c.m = djl;
                         c.k1 = djr;
                         c.k2 = dr;
@@ -346,17 +476,50 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     int maxd = std::max({XL.basis.dmax(), OL.basis.dmax(), 1});
     ensure_ident(P, maxd);
     const int64_t cap = scratch_cap(P);
-    pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, 1 << 14);
-    ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
-    pl.upload(P.stream);
-    BufTable bt{};
-    bt.p[BUF_L] = X.d;
-    bt.p[BUF_R] = out->d;
-    bt.p[BUF_INT] = d_int;
-    bt.p[BUF_PSI] = A.d;
-    bt.p[BUF_SCR] = P.d_scratch;
-    bt.p[BUF_ID] = P.d_ident;
-    pl.run(bt, 1, P.stream);
+    if (P.mixed()) {
+        pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F32);
+        P.stats.ms_host_plan += host_ms_since(host0);
+        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 8));
+        pl.upload(P.stream);
+        float* acc = alloc_f32(P, out->n);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, out->n * 4, P.stream));
+        TcBufs tb = tc_base(P);
+        tb.hi[BUF_L] = X.h;
+        tb.lo[BUF_L] = X.l;
+        tb.hi[BUF_INT] = IS.h;
+        tb.lo[BUF_INT] = IS.l;
+        tb.hi[BUF_PSI] = A.h;
+        tb.lo[BUF_PSI] = A.l;
+        tb.hi[BUF_SCR] = P.s_hi;
+        tb.lo[BUF_SCR] = P.s_lo;
+        tb.hi[BUF_ID] = P.id_hi;
+        tb.lo[BUF_ID] = P.id_lo;
+        tb.out[BUF_R] = acc;
+        tb.out[BUF_SCR] = P.s_hi;
+        tb.out_lo[BUF_SCR] = P.s_lo;
+        pl.run_tc(tb, 1, P.nsplit, P.stream);
+        P.check_device_error();
+        out->h = P.alloc_bf16(out->n);
+        out->l = P.alloc_bf16(out->n);
+        dev_split_f32(acc, out->n, out->h, out->l, P.stream);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+        free_f32(P, acc, out->n);
+    } else {
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, kChunkF64);
+        P.stats.ms_host_plan += host_ms_since(host0);
+        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
+        pl.upload(P.stream);
+        out->d = P.alloc(out->n);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(out->d, 0, out->n * 8, P.stream));
+        BufTable bt{};
+        bt.p[BUF_L] = X.d;
+        bt.p[BUF_R] = out->d;
+        bt.p[BUF_INT] = IS.d;
+        bt.p[BUF_PSI] = A.d;
+        bt.p[BUF_SCR] = P.d_scratch;
+        bt.p[BUF_ID] = P.d_ident;
+        pl.run(bt, 1, P.stream);
+    }
     cudaEventRecord(e1, P.stream);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     float ms = 0.f;
@@ -364,8 +527,8 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     P.stats.ms_renorm += ms;
     P.stats.renorm_flops_last = pl.flops + fl_int;
     pl.release();
-    P.free(d_int, n_int);
-    P.free(A.d, A.n);
+    free_interms(P, IS);
+    free_site(P, A);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return out;
@@ -377,28 +540,22 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
 
 void ensure_env(Plan& P, int k) {
     const int K = P.K;
-    // left[k-1]
     if (!P.left[0]) P.left[0] = make_vacuum(P, false);
-    int m = k - 1;
+    const int m = k - 1;
     int have = m;
     while (have > 0 && !P.left[have]) --have;
+    // keep the block next to the new one (a step back needs it) and free the rest
     for (int j = have + 1; j <= m; ++j) {
         P.left[j] = renormalise(P, *P.left[j - 1], j, true);
-        if (!P.opt.keep_envs && j - 1 >= 1) {
-            P.free(P.left[j - 1]->d, P.left[j - 1]->n);
-            P.left[j - 1].reset();
-        }
+        if (!P.opt.keep_envs && j - 1 >= 1 && j - 1 < m - 1) free_block(P, P.left[j - 1]);
     }
     if (!P.right[K]) P.right[K] = make_vacuum(P, true);
-    int mr = k + 1;
+    const int mr = k + 1;
     int haver = mr;
     while (haver < K && !P.right[haver]) ++haver;
     for (int j = haver - 1; j >= mr; --j) {
         P.right[j] = renormalise(P, *P.right[j + 1], j + 1, false);
-        if (!P.opt.keep_envs && j + 1 <= K - 1) {
-            P.free(P.right[j + 1]->d, P.right[j + 1]->n);
-            P.right[j + 1].reset();
-        }
+        if (!P.opt.keep_envs && j + 1 <= K - 1 && j + 1 > mr + 1) free_block(P, P.right[j + 1]);
     }
 }
 
@@ -409,18 +566,20 @@ void build_layout(Plan& P, int k) {
     const auto& br = P.mps.bonds[k + 1];
     std::map<std::pair<int, int>, int> ridx;
     for (int i = 0; i < (int)br.size(); ++i) ridx[{br[i][0], br[i][1]}] = i;
-    int64_t off = 0;
+    int64_t off = 0, poff = 0;
     for (int il = 0; il < (int)bl.size(); ++il)
         for (int y = 0; y < 16; ++y) {
             QN q = QN(bl[il][0], bl[il][1]) + kSiteQN[y / 4] + kSiteQN[y % 4];
             auto it = ridx.find({q.n, q.s});
             if (it == ridx.end()) continue;
-            Plan::Sector s{il, y, it->second, off, bl[il][2], br[it->second][2]};
+            Plan::Sector s{il, y, it->second, off, bl[il][2], br[it->second][2], poff};
             P.sector_of[{il, y}] = (int)P.layout.size();
             P.layout.push_back(s);
             off += (int64_t)s.dl * s.dr;
+            poff += (int64_t)s.dl * round_up(s.dr, 8);
         }
     P.dim = off;
+    P.dim_pad = std::max<int64_t>(poff, 8);
 }
 
 void set_bond(Plan& P, int k) {
@@ -438,7 +597,7 @@ void set_bond(Plan& P, int k) {
     cudaEventRecord(e0, P.stream);
     const Block* blocks[2] = {&L, &R};
     double fl = 0.0;
-    form_interms(P, P.sp.interms, blocks, P.d_interm, P.n_interm, fl);
+    form_interms(P, P.sp.interms, blocks, P.interm, fl);
     cudaEventRecord(e1, P.stream);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     float ms = 0.f;
@@ -447,21 +606,21 @@ void set_bond(Plan& P, int k) {
     cudaEventDestroy(e1);
     P.stats.ms_interm += ms;
     P.stats.interm_flops = fl;
-    P.stats.interm_bytes = P.n_interm * 8;
-    P.stats.store_bytes = (L.n + R.n) * 8;
+    P.stats.interm_bytes = P.interm.n * (P.mixed() ? 4 : 8);
+    P.stats.store_bytes = (L.n + R.n) * (P.mixed() ? 4 : 8);
 
-    // sigma contributions
+    // sigma contributions (FP64 views; the bf16 copy of psi is padded)
+    const auto hs0 = std::chrono::steady_clock::now();
     ProductList& pl = P.sigma_pl;
     pl.clear();
-    for (const Plan::Sector& s : P.layout) {
-        pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
-    }
+    for (const Plan::Sector& s : P.layout) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
     const LocalOps& Y = P.sp.y;
     int64_t nitems = 0;
     for (const Term3& t : P.sp.terms) {
         const LocalOp& M = Y.ops[t.y];
         const int pR = ref_parity(R.lay, P.sp.interms, t.R);
-        for (const Plan::Sector& s : P.layout) {
+        for (size_t si = 0; si < P.layout.size(); ++si) {
+            const Plan::Sector& s = P.layout[si];
             OpLookup ol = lookup(L.lay, P.sp.interms, t.L, s.il, BUF_L);
             if (!ol.ok) continue;
             OpLookup orr = lookup(R.lay, P.sp.interms, t.R, s.ir, BUF_R);
@@ -469,15 +628,14 @@ void set_bond(Plan& P, int k) {
             const int nl = L.lay.basis.qn[s.il].n;
             const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
             for (int y2 = 0; y2 < 16; ++y2) {
-                double mv = M.at(y2, s.y);
+                const double mv = M.at(y2, s.y);
                 if (mv == 0.0) continue;
                 auto it = P.sector_of.find({ol.j, y2});
-                DMRG_REQUIRE(it != P.sector_of.end() || true, DMRG_EINVAL, "");
                 if (it == P.sector_of.end()) continue;
                 const Plan::Sector& o = P.layout[it->second];
                 DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
-                int e = M.parity * nl + pR * (nl + ny);
-                double zeta = (e & 1) ? -1.0 : 1.0;
+                const int e = M.parity * nl + pR * (nl + ny);
+                const double zeta = (e & 1) ? -1.0 : 1.0;
                 Contrib c;
                 c.out = it->second;
                 c.P = ol.v;  // O^L_eff : d_jl x d_il
@@ -485,12 +643,12 @@ void set_bond(Plan& P, int k) {
                 c.Q.off = s.off;
                 c.Q.ld = s.dr;  // Psi_s : d_il x d_ir
                 c.R = orr.v.T();  // (O^R_eff)^T : d_ir x d_jr
-                c.R.ident = orr.v.ident;
                 c.m = o.dl;
                 c.k1 = s.dl;
                 c.k2 = s.dr;
                 c.n = o.dr;
                 c.alpha = t.c * zeta * mv;
+                c.qsec = (int)si;
                 pl.cs.push_back(c);
                 ++nitems;
             }
@@ -498,12 +656,41 @@ void set_bond(Plan& P, int k) {
     }
     int maxd = std::max({L.lay.basis.dmax(), R.lay.basis.dmax(), 1});
     ensure_ident(P, maxd);
-    pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), 1 << 14);
-    ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
-    pl.upload(P.stream);
+    P.sigma_fp64_ready = false;
+    if (P.mixed()) {
+        ProductList& tl = P.sigma_tc;
+        tl.clear();
+        tl.outs = pl.outs;
+        tl.cs = pl.cs;
+        for (Contrib& c : tl.cs) {
+            const Plan::Sector& s = P.layout[c.qsec];
+            c.Q.off = s.poff;
+            c.Q.ld = (int)round_up(s.dr, 8);
+        }
+        tl.lower_tc(BUF_SCR, BUF_ID, P.id_n, scratch_cap(P), kChunkTC, TC_ATOMIC_F64);
+        tl.cs.clear();
+        ensure_scratch(P, std::max<int64_t>(tl.scratch_elems, 8));
+        tl.upload(P.stream);
+        P.stats.sigma_flops = tl.flops;
+        // padded bf16 copy of psi: one split job per sector
+        std::vector<SplitJob> jobs;
+        for (const Plan::Sector& s : P.layout)
+            jobs.push_back({s.off, s.poff, s.dl, s.dr, s.dr, (int)round_up(s.dr, 8)});
+        if (P.d_psi_jobs) cudaFree(P.d_psi_jobs);
+        P.n_psi_jobs = (int)jobs.size();
+        DMRG_CHECK_CUDA(cudaMalloc(&P.d_psi_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(SplitJob)));
+        if (!jobs.empty())
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_psi_jobs, jobs.data(), jobs.size() * sizeof(SplitJob),
+                                            cudaMemcpyHostToDevice, P.stream));
+    } else {
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), kChunkF64);
+        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
+        pl.upload(P.stream);
+        P.sigma_fp64_ready = true;
+        P.stats.sigma_flops = pl.flops;
+    }
     P.stats.n_terms = (int64_t)P.sp.terms.size();
     P.stats.n_items = nitems;
-    P.stats.sigma_flops = pl.flops;
 
     // diag(H_eff): terms whose three factors all conserve the quantum numbers
     ProductList& hl = P.hdiag_pl;
@@ -517,7 +704,7 @@ void set_bond(Plan& P, int k) {
             const int pR = ref_parity(R.lay, P.sp.interms, t.R);
             for (size_t si = 0; si < P.layout.size(); ++si) {
                 const Plan::Sector& s = P.layout[si];
-                double mv = M.at(s.y, s.y);
+                const double mv = M.at(s.y, s.y);
                 if (mv == 0.0) continue;
                 OpLookup ol = lookup(L.lay, P.sp.interms, t.L, s.il, BUF_L);
                 if (!ol.ok || ol.j != s.il) continue;
@@ -525,8 +712,8 @@ void set_bond(Plan& P, int k) {
                 if (!orr.ok || orr.j != s.ir) continue;
                 const int nl = L.lay.basis.qn[s.il].n;
                 const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
-                int e = M.parity * nl + pR * (nl + ny);
-                double zeta = (e & 1) ? -1.0 : 1.0;
+                const int e = M.parity * nl + pR * (nl + ny);
+                const double zeta = (e & 1) ? -1.0 : 1.0;
                 View a = ol.v, b = orr.v;
                 if (a.ident) {
                     a.buf = BUF_ID;
@@ -560,15 +747,29 @@ void set_bond(Plan& P, int k) {
         hl.chunks.emplace_back(WorkList(), std::move(w));
         hl.upload(P.stream);
     }
+    P.stats.ms_host_plan += host_ms_since(hs0);
     P.bond = k;
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
 }
 
+// FP64 engine tables (the operator buffers are bf16 pieces in mixed mode)
 BufTable bond_buffers(Plan& P, const double* psi, double* out) {
     BufTable bt{};
-    bt.p[BUF_L] = P.left[P.bond - 1]->d;
-    bt.p[BUF_R] = P.right[P.bond + 1]->d;
-    bt.p[BUF_INT] = P.d_interm;
+    const Block& L = *P.left[P.bond - 1];
+    const Block& R = *P.right[P.bond + 1];
+    if (P.mixed()) {
+        bt.p[BUF_L] = (double*)L.h;
+        bt.lo[BUF_L] = L.l;
+        bt.p[BUF_R] = (double*)R.h;
+        bt.lo[BUF_R] = R.l;
+        bt.p[BUF_INT] = (double*)P.interm.h;
+        bt.lo[BUF_INT] = P.interm.l;
+        bt.pmask = (1u << BUF_L) | (1u << BUF_R) | (1u << BUF_INT);
+    } else {
+        bt.p[BUF_L] = L.d;
+        bt.p[BUF_R] = R.d;
+        bt.p[BUF_INT] = P.interm.d;
+    }
     bt.p[BUF_PSI] = const_cast<double*>(psi);
     bt.p[BUF_SCR] = P.d_scratch;
     bt.p[BUF_ID] = P.d_ident;
@@ -579,21 +780,85 @@ BufTable bond_buffers(Plan& P, const double* psi, double* out) {
     return bt;
 }
 
+// sigma in FP64 arithmetic over the stored operators (exact upcast of the
+// bf16 pieces in mixed mode)
+void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
+    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
+    if (!P.sigma_fp64_ready) {
+        P.sigma_pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap(P) / 2, 1 << 24), kChunkF64);
+        ensure_scratch_f64(P, std::max<int64_t>(P.sigma_pl.scratch_elems, 1));
+        P.sigma_pl.upload(st);
+        P.sigma_fp64_ready = true;
+    }
+    const int64_t per = std::max<int64_t>(P.sigma_pl.scratch_elems, 1);
+    for (int v = 0; v < nvec; ++v) {
+        DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v * P.dim, 0, (size_t)P.dim * 8, st));
+        BufTable bt = bond_buffers(P, psi + (int64_t)v * P.dim, out + (int64_t)v * P.dim);
+        bt.vstride[BUF_SCR] = per;
+        P.sigma_pl.run(bt, 1, st);
+    }
+}
+
 void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
     DMRG_REQUIRE(nvec >= 1, DMRG_EINVAL, "nvec must be >= 1");
-    // scratch is per vector: run in groups that fit
-    int64_t per = std::max<int64_t>(P.sigma_pl.scratch_elems, 1);
-    int group = (int)std::max<int64_t>(1, std::min<int64_t>(nvec, P.n_scratch / per));
+    if (!P.mixed()) {
+        const int64_t per = std::max<int64_t>(P.sigma_pl.scratch_elems, 1);
+        const int group = (int)std::max<int64_t>(1, std::min<int64_t>(nvec, P.n_scratch / per));
+        for (int v0 = 0; v0 < nvec; v0 += group) {
+            const int nv = std::min(group, nvec - v0);
+            DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v0 * P.dim, 0, (size_t)nv * P.dim * 8, st));
+            BufTable bt = bond_buffers(P, psi + (int64_t)v0 * P.dim, out + (int64_t)v0 * P.dim);
+            bt.vstride[BUF_SCR] = per;
+            P.sigma_pl.run(bt, nv, st);
+        }
+        P.stats.sigma_calls += nvec;
+        return;
+    }
+    // mixed precision: bf16 pieces of psi, tensor-core products, FP64 accumulation of sigma
+    const ProductList& tl = P.sigma_tc;
+    const int64_t per = std::max<int64_t>(tl.scratch_elems, 8);
+    const int group = (int)std::max<int64_t>(1, std::min<int64_t>(nvec, P.n_spc / per));
+    const int64_t need_psi = (int64_t)group * P.dim_pad;
+    if (need_psi > P.n_ppc) {
+        P.free_bf16(P.ps_hi, P.n_ppc);
+        P.free_bf16(P.ps_lo, P.n_ppc);
+        P.n_ppc = need_psi;
+        P.ps_hi = P.alloc_bf16(need_psi);
+        P.ps_lo = P.alloc_bf16(need_psi);
+    }
+    const Block& L = *P.left[P.bond - 1];
+    const Block& R = *P.right[P.bond + 1];
     for (int v0 = 0; v0 < nvec; v0 += group) {
-        int nv = std::min(group, nvec - v0);
+        const int nv = std::min(group, nvec - v0);
+        for (int v = 0; v < nv; ++v)
+            dev_split_blocks(psi + (int64_t)(v0 + v) * P.dim, P.d_psi_jobs, P.n_psi_jobs,
+                             P.ps_hi + (int64_t)v * P.dim_pad, P.ps_lo + (int64_t)v * P.dim_pad, st);
         DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v0 * P.dim, 0, (size_t)nv * P.dim * 8, st));
-        if (nv > 1) ensure_scratch(P, per * nv);
-        BufTable bt = bond_buffers(P, psi + (int64_t)v0 * P.dim, out + (int64_t)v0 * P.dim);
-        bt.vstride[BUF_SCR] = per;
-        P.sigma_pl.run(bt, nv, st);
+        TcBufs tb = tc_base(P);
+        tb.hi[BUF_L] = L.h;
+        tb.lo[BUF_L] = L.l;
+        tb.hi[BUF_R] = R.h;
+        tb.lo[BUF_R] = R.l;
+        tb.hi[BUF_INT] = P.interm.h;
+        tb.lo[BUF_INT] = P.interm.l;
+        tb.hi[BUF_PSI] = P.ps_hi;
+        tb.lo[BUF_PSI] = P.ps_lo;
+        tb.vstride[BUF_PSI] = P.dim_pad;
+        tb.hi[BUF_SCR] = P.s_hi;
+        tb.lo[BUF_SCR] = P.s_lo;
+        tb.vstride[BUF_SCR] = per;
+        tb.hi[BUF_ID] = P.id_hi;
+        tb.lo[BUF_ID] = P.id_lo;
+        tb.out[BUF_OUT] = out + (int64_t)v0 * P.dim;
+        tb.out_vstride[BUF_OUT] = P.dim;
+        tb.out[BUF_SCR] = P.s_hi;
+        tb.out_lo[BUF_SCR] = P.s_lo;
+        tb.out_vstride[BUF_SCR] = per;
+        P.sigma_tc.run_tc(tb, nv, P.nsplit, st);
     }
     P.stats.sigma_calls += nvec;
+    P.check_device_error();
 }
 
 void hdiag(Plan& P, double* out, cudaStream_t st) {

@@ -5,10 +5,12 @@
 
 namespace dmrg {
 
-void form_interms(Plan& P, Interms& im, const Block* blocks[2], double*& d_int, int64_t& n_int,
-                  double& flops);
+void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops);
+void free_interms(Plan& P, IntermStore& S);
+void free_block(Plan& P, std::unique_ptr<Block>& b);
 void ensure_ident(Plan& P, int n);
-void ensure_scratch(Plan& P, int64_t n);
+void ensure_scratch(Plan& P, int64_t n);      // scratch of the plan's engine
+void ensure_scratch_f64(Plan& P, int64_t n);  // FP64 scratch (FP64 engine in either mode)
 int64_t scratch_cap(const Plan& P);
 std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end);
 Basis bond_basis(const Plan& P, int b, bool right_side);
@@ -17,7 +19,10 @@ void ensure_env(Plan& P, int k);
 void build_layout(Plan& P, int k);
 void set_bond(Plan& P, int k);
 BufTable bond_buffers(Plan& P, const double* psi, double* out);
+// sigma with the plan's engine (tensor cores in mixed precision)
 void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
+// sigma in FP64 arithmetic over the stored operators (either precision)
+void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
 void hdiag(Plan& P, double* out, cudaStream_t st);
 
 // solver.cu

@@ -140,7 +140,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->max_iter = 200;
     o->max_space = 0;
     o->precond = DMRG_PRECOND_JACOBI;
-    o->fp64_final = 1;
+    o->fp64_final = 0;
     o->mem_budget = 0;
     o->scratch_bytes = 0;
     o->keep_envs = 0;
@@ -148,7 +148,7 @@ void dmrg_default_options(dmrg_options* o) {
 }
 
 const char* dmrg_version(void) {
-    return "libdmrg 0.1 (sm_103a; FP64 segmented grouped GEMM)";
+    return "libdmrg 0.2 (sm_103a; FP64 segmented grouped GEMM; tcgen05 bf16-piece engine)";
 }
 
 dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_core, int K, int N, int twoS,
@@ -169,8 +169,10 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         Plan& P = plan->P;
         if (opt) P.opt = *opt;
         else dmrg_default_options(&P.opt);
-        if (P.opt.precision != DMRG_FP64)
-            throw Error(DMRG_EINVAL, "precision mode not available in this build");
+        if (P.opt.precision == DMRG_FP64) P.nsplit = 0;
+        else if (P.opt.precision == DMRG_BF16X3) P.nsplit = 2;
+        else if (P.opt.precision == DMRG_BF16) P.nsplit = 1;
+        else throw Error(DMRG_EINVAL, "unknown precision mode");
         P.K = K;
         P.N = N;
         P.twoS = twoS;
@@ -281,6 +283,17 @@ dmrg_status dmrg_sigma(dmrg_plan_t plan, const double* psi, double* sig, int nve
         P.stats.ms_gemm += ms;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_sigma_fp64(dmrg_plan_t plan, const double* psi, double* sig, int nvec, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || !sig || nvec < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        sigma_fp64(plan->P, psi, sig, nvec, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
         return DMRG_OK;
     });
 }

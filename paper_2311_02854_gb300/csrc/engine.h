@@ -39,6 +39,10 @@ constexpr int kMaxBufs = 8;
 struct BufTable {
     double* p[kMaxBufs];
     int64_t vstride[kMaxBufs];
+    // buffers whose bit is set in pmask hold bf16 pieces: p[i] is the hi piece
+    // (as raw bf16) and lo[i] the lo piece (may be null); they are read as hi + lo.
+    const void* lo[kMaxBufs];
+    uint32_t pmask;
 };
 
 // A work list in host memory plus its device copy.

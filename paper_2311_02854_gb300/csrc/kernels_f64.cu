@@ -2,6 +2,8 @@
 // the sigma step, the renormalisation, the intermediates and the density
 // matrices; Sec. 2.2 "GEMM step" with the "reduction" fused into the
 // accumulator) and the vector / Jacobi kernels of Davidson and decimation.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "engine.h"
@@ -98,6 +100,17 @@ void WorkList::release() {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+// element idx of buffer buf (FP64, or bf16 pieces read as hi + lo)
+__device__ __forceinline__ double ld_elem(const BufTable& bt, int buf, int64_t idx) {
+    if (bt.pmask & (1u << buf)) {
+        const __nv_bfloat16* h = (const __nv_bfloat16*)bt.p[buf];
+        double x = (double)__bfloat162float(h[idx]);
+        if (bt.lo[buf]) x += (double)__bfloat162float(((const __nv_bfloat16*)bt.lo[buf])[idx]);
+        return x;
+    }
+    return bt.p[buf][idx];
+}
+
 __global__ void __launch_bounds__(NT) seg_gemm_f64_kernel(const Tile* __restrict__ tiles,
                                                           const Seg* __restrict__ segs, BufTable bt) {
     const Tile T = tiles[blockIdx.x];
@@ -114,8 +127,8 @@ __global__ void __launch_bounds__(NT) seg_gemm_f64_kernel(const Tile* __restrict
     const int mrem = T.m - T.m0, nrem = T.n - T.n0;
     for (int s = T.seg_beg; s < T.seg_end; ++s) {
         const Seg S = segs[s];
-        const double* A = bt.p[S.a_buf] + S.a_off + (int64_t)v * bt.vstride[S.a_buf];
-        const double* B = bt.p[S.b_buf] + S.b_off + (int64_t)v * bt.vstride[S.b_buf];
+        int64_t A = S.a_off + (int64_t)v * bt.vstride[S.a_buf];
+        int64_t B = S.b_off + (int64_t)v * bt.vstride[S.b_buf];
         A += S.a_tr ? (int64_t)T.m0 : (int64_t)T.m0 * S.lda;
         B += S.b_tr ? (int64_t)T.n0 * S.ldb : (int64_t)T.n0;
         for (int k0 = 0; k0 < S.k; k0 += BK) {
@@ -131,7 +144,8 @@ __global__ void __launch_bounds__(NT) seg_gemm_f64_kernel(const Tile* __restrict
                 }
                 double x = 0.0;
                 if (m < mrem && k0 + kk < S.k)
-                    x = S.a_tr ? A[(int64_t)(k0 + kk) * S.lda + m] : A[(int64_t)m * S.lda + k0 + kk];
+                    x = ld_elem(bt, S.a_buf,
+                                A + (S.a_tr ? (int64_t)(k0 + kk) * S.lda + m : (int64_t)m * S.lda + k0 + kk));
                 As[kk][m] = x * S.alpha;
             }
 #pragma unroll
@@ -146,7 +160,8 @@ __global__ void __launch_bounds__(NT) seg_gemm_f64_kernel(const Tile* __restrict
                 }
                 double x = 0.0;
                 if (n < nrem && k0 + kk < S.k)
-                    x = S.b_tr ? B[(int64_t)n * S.ldb + k0 + kk] : B[(int64_t)(k0 + kk) * S.ldb + n];
+                    x = ld_elem(bt, S.b_buf,
+                                B + (S.b_tr ? (int64_t)n * S.ldb + k0 + kk : (int64_t)(k0 + kk) * S.ldb + n));
                 Bs[kk][n] = x;
             }
             __syncthreads();

@@ -151,12 +151,69 @@ void Plan::free(double*& p, int64_t n) {
     p = nullptr;
 }
 
+__nv_bfloat16* Plan::alloc_bf16(int64_t n) {
+    if (n <= 0) return nullptr;
+    int64_t bytes = round_up(n * 2, 256);
+    DMRG_REQUIRE(budget <= 0 || dev_bytes + bytes <= budget, DMRG_ENOMEM,
+                 "device budget exceeded (" + std::to_string((dev_bytes + bytes) >> 20) + " MiB)");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(DMRG_ENOMEM, "cudaMalloc of " + std::to_string(bytes >> 20) + " MiB failed");
+    }
+    dev_bytes += bytes;
+    stats.device_bytes = dev_bytes;
+    return (__nv_bfloat16*)p;
+}
+
+void Plan::free_bf16(__nv_bfloat16*& p, int64_t n) {
+    if (p) {
+        cudaFree(p);
+        dev_bytes -= round_up(n * 2, 256);
+        stats.device_bytes = dev_bytes;
+    }
+    p = nullptr;
+}
+
+void Plan::check_device_error() {
+    if (!d_ctr) return;
+    int err = 0;
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(&err, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(stream));
+    if (err) {
+        DMRG_CHECK_CUDA(cudaMemsetAsync(d_ctr + 1, 0, sizeof(int), stream));
+        throw Error(DMRG_ETIMEOUT, "a tensor-core kernel gave up waiting (device error word set)");
+    }
+}
+
 Plan::~Plan() {
     for (auto& b : left)
-        if (b && b->d) free(b->d, b->n);
+        if (b) {
+            if (b->d) free(b->d, b->n);
+            free_bf16(b->h, b->n);
+            free_bf16(b->l, b->n);
+        }
     for (auto& b : right)
-        if (b && b->d) free(b->d, b->n);
-    free(d_interm, n_interm);
+        if (b) {
+            if (b->d) free(b->d, b->n);
+            free_bf16(b->h, b->n);
+            free_bf16(b->l, b->n);
+        }
+    free_bf16(s_hi, n_spc);
+    free_bf16(s_lo, n_spc);
+    free_bf16(ps_hi, n_ppc);
+    free_bf16(ps_lo, n_ppc);
+    free_bf16(id_hi, (int64_t)id_n * id_n);
+    free_bf16(id_lo, (int64_t)id_n * id_n);
+    free_bf16(w_hi, n_wpc);
+    free_bf16(w_lo, n_wpc);
+    if (d_psi_jobs) cudaFree(d_psi_jobs);
+    if (d_ctr) cudaFree(d_ctr);
+    sigma_tc.release();
+    free(interm.d, interm.n);
+    free_bf16(interm.h, interm.n);
+    free_bf16(interm.l, interm.n);
     free(d_scratch, n_scratch);
     free(d_ident, (int64_t)ident_n * ident_n);
     free(d_wcoef, n_wcoef);
@@ -202,7 +259,9 @@ static Seg make_seg(const View& A, const View& B, int k, double alpha) {
     return s;
 }
 
-void ProductList::lower(int8_t sbuf, int8_t ibuf, int ild, int64_t cap, int64_t kchunk) {
+void ProductList::lower(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t kchunk) {
+    const int8_t sbuf = sbuf_;
+    this->sbuf = sbuf_;
     release();
     chunks.clear();
     flops = 0.0;
@@ -273,6 +332,117 @@ void ProductList::lower(int8_t sbuf, int8_t ibuf, int ild, int64_t cap, int64_t 
     }
 }
 
+void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t kchunk, uint8_t out_mode) {
+    const int8_t sbuf = sbuf_;
+    this->sbuf = sbuf_;
+    release();
+    chunks.clear();
+    flops = 0.0;
+    scratch_elems = 0;
+    tc = true;
+    View I;
+    I.buf = ibuf;
+    I.off = 0;
+    I.ld = ild;
+    size_t i = 0;
+    while (i < cs.size()) {
+        WorkList p1, p2;
+        std::map<int, std::vector<Seg>> segs;
+        std::vector<int> order;
+        int64_t used = 0;
+        for (; i < cs.size(); ++i) {
+            const Contrib& c = cs[i];
+            const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
+            const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
+            // scratch needed by this contribution
+            int64_t need = 0;
+            bool pq_first = true;
+            double cost = 0.0;
+            int tr = 0, tc_ = 0;  // rows / cols of the phase-1 product
+            if (nreal == 3) {
+                double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                pq_first = cost_pq <= cost_qr;
+                cost = std::min(cost_pq, cost_qr);
+                tr = pq_first ? c.m : c.k1;
+                tc_ = pq_first ? c.k2 : c.n;
+            } else if (!unit) {
+                tr = c.m;
+                tc_ = c.n;
+            }
+            if (tr > 0) need = (int64_t)tr * round_up(tc_, 8);
+            if (used + need > cap && used > 0) break;
+            if (!segs.count(c.out)) order.push_back(c.out);
+            std::vector<Seg>& sv = segs[c.out];
+            View T;
+            T.buf = sbuf;
+            T.off = used;
+            T.ld = (int)round_up(std::max(tc_, 1), 8);
+            if (nreal == 3) {
+                flops += cost;
+                if (pq_first) {
+                    p1.add_block(used, sbuf, c.m, c.k2, T.ld, {make_seg(c.P, c.Q, c.k1, 1.0)}, TC_STORE_SPLIT, 0, 128,
+                                 (float)c.alpha);
+                    sv.push_back(make_seg(T, c.R, c.k2, 1.0));
+                } else {
+                    p1.add_block(used, sbuf, c.k1, c.n, T.ld, {make_seg(c.Q, c.R, c.k2, 1.0)}, TC_STORE_SPLIT, 0, 128,
+                                 (float)c.alpha);
+                    sv.push_back(make_seg(c.P, T, c.k1, 1.0));
+                }
+                used += need;
+                continue;
+            }
+            // the two (or one) real factors X (m x k) and Y (k x n)
+            View X, Y;
+            int k;
+            if (nreal == 2) {
+                if (c.P.ident) {
+                    X = c.Q;
+                    Y = c.R;
+                    k = c.k2;
+                } else if (c.R.ident) {
+                    X = c.P;
+                    Y = c.Q;
+                    k = c.k1;
+                } else {
+                    X = c.P;
+                    Y = c.R;
+                    k = c.k1;
+                }
+                flops += 2.0 * c.m * c.n * k;
+            } else {
+                X = !c.P.ident ? c.P : (!c.Q.ident ? c.Q : c.R);
+                Y = I;
+                k = c.n;
+                flops += 2.0 * c.m * c.n;
+            }
+            if (unit) {
+                sv.push_back(make_seg(X, Y, k, c.alpha));
+            } else {
+                p1.add_block(used, sbuf, c.m, c.n, T.ld, {make_seg(X, Y, k, 1.0)}, TC_STORE_SPLIT, 0, 128,
+                             (float)c.alpha);
+                sv.push_back(make_seg(T, I, c.n, 1.0));
+                used += need;
+            }
+        }
+        for (int o : order) {
+            const OutBlock& ob = outs[o];
+            p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 128, 1.0f);
+        }
+        scratch_elems = std::max(scratch_elems, used);
+        chunks.emplace_back(std::move(p1), std::move(p2));
+    }
+}
+
+void ProductList::run_tc(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st) {
+    for (auto& c : chunks) {
+        DMRG_REQUIRE(c.first.tiles.empty() || (sbuf >= 0 && tb.hi[sbuf] && tb.out[sbuf]), DMRG_EINVAL,
+                     "tensor-core product list run without its scratch buffer");
+        launch_seg_gemm_tc(c.first, tb, nvec, nsplit, st);
+        launch_seg_gemm_tc(c.second, tb, nvec, nsplit, st);
+    }
+}
+
 void ProductList::upload(cudaStream_t st) {
     for (auto& c : chunks) {
         c.first.upload(st);
@@ -282,6 +452,8 @@ void ProductList::upload(cudaStream_t st) {
 
 void ProductList::run(const BufTable& bt, int nvec, cudaStream_t st) {
     for (auto& c : chunks) {
+        DMRG_REQUIRE(c.first.tiles.empty() || (sbuf >= 0 && bt.p[sbuf]), DMRG_EINVAL,
+                     "product list run without its scratch buffer");
         launch_seg_gemm_f64(c.first, bt, nvec, st);
         launch_seg_gemm_f64(c.second, bt, nvec, st);
     }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "tc.h"
 #include "symbolic.h"
 
 namespace dmrg {
@@ -44,6 +45,7 @@ struct Contrib {
     View P, Q, R;
     int m, k1, k2, n;
     double alpha;
+    int qsec = -1;  // sigma: wavefunction sector read by Q (for the padded bf16 copy)
 };
 struct OutBlock {
     int8_t buf;
@@ -59,16 +61,34 @@ struct ProductList {
     std::vector<std::pair<WorkList, WorkList>> chunks;
     double flops = 0.0;  // algorithmic
     int64_t scratch_elems = 0;
+    int8_t sbuf = -1;  // buffer id of the phase-1 scratch
+    bool tc = false;
     void clear();
+    // FP64 engine: per-segment alpha, 64x64 tiles
     void lower(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk);
+    // tensor-core engine: alpha folded into phase-1 products (or a sign bit), 128x128 tiles;
+    // phase-1 products are stored as bf16 pieces with rows padded to 8
+    void lower_tc(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk,
+                  uint8_t out_mode);
     void upload(cudaStream_t st);
     void run(const BufTable& bt, int nvec, cudaStream_t st);
+    void run_tc(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st);
     void release();
+};
+
+// Intermediates of a bond or of a renormalisation step (FP64 or bf16 pieces).
+struct IntermStore {
+    double* d = nullptr;
+    __nv_bfloat16* h = nullptr;
+    __nv_bfloat16* l = nullptr;
+    int64_t n = 0;
 };
 
 struct Block {
     BlockLayout lay;
-    double* d = nullptr;
+    double* d = nullptr;         // FP64 store
+    __nv_bfloat16* h = nullptr;  // bf16 pieces (mixed precision)
+    __nv_bfloat16* l = nullptr;
     int64_t n = 0;
 };
 
@@ -78,6 +98,8 @@ struct Plan {
     MPSHost mps;
     QN tot;
     int K = 0, N = 0, twoS = 0, D = 0, n_so = 0;
+    int nsplit = 0;  // 0: FP64 engine; 1: bf16; 2: bf16 x3 (hi + lo)
+    bool mixed() const { return nsplit > 0; }
     cudaStream_t stream = nullptr;
     std::string last_error;
     dmrg_stats_t stats{};
@@ -91,20 +113,35 @@ struct Plan {
         int il, y, ir;
         int64_t off;
         int dl, dr;
+        int64_t poff;  // offset in the padded (rows of round8(dr)) copy
     };
     std::vector<Sector> layout;
     std::map<std::pair<int, int>, int> sector_of;  // (il, y) -> sector
-    int64_t dim = 0;
+    int64_t dim = 0, dim_pad = 0;
     SigmaPlan sp;
-    double* d_interm = nullptr;
-    int64_t n_interm = 0;
-    ProductList sigma_pl, hdiag_pl;
+    IntermStore interm;  // the bond's intermediates
+    ProductList sigma_pl, hdiag_pl, sigma_tc;
     double* d_scratch = nullptr;
     int64_t n_scratch = 0;
     double* d_ident = nullptr;
     int ident_n = 0;
     double* d_wcoef = nullptr;
     int64_t n_wcoef = 0;
+
+    // mixed precision: bf16 pieces (hi, lo) of scratch, wavefunction,
+    // identity, coefficient matrices and intermediates
+    __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;
+    int64_t n_spc = 0;
+    __nv_bfloat16 *ps_hi = nullptr, *ps_lo = nullptr;
+    int64_t n_ppc = 0;
+    __nv_bfloat16 *id_hi = nullptr, *id_lo = nullptr;
+    int id_n = 0;
+    __nv_bfloat16 *w_hi = nullptr, *w_lo = nullptr;
+    int64_t n_wpc = 0;
+    SplitJob* d_psi_jobs = nullptr;
+    int n_psi_jobs = 0;
+    int* d_ctr = nullptr;  // [0] tile counter, [1] device error word
+    bool sigma_fp64_ready = false;
 
     // host-buffer entry point
     double* d_io = nullptr;
@@ -119,6 +156,9 @@ struct Plan {
 
     double* alloc(int64_t n);
     void free(double*& p, int64_t n);
+    __nv_bfloat16* alloc_bf16(int64_t n);
+    void free_bf16(__nv_bfloat16*& p, int64_t n);
+    void check_device_error();
     ~Plan();
 };
 

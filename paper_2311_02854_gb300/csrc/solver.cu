@@ -191,6 +191,16 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
         }
     }
     DMRG_CHECK_CUDA(cudaMemcpyAsync(psi, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+    if (P.mixed() && P.opt.fp64_final) {
+        // FP64 Rayleigh quotients <x|H|x> of the mixed-precision Ritz vectors
+        for (int i = 0; i < nr; ++i) {
+            double* xi = X + (int64_t)i * n;
+            sigma_fp64(P, xi, WY, 1, st);
+            const double num = host_dot(P, xi, WY, n, dco, dwork);
+            const double den = host_dot(P, xi, xi, n, dco, dwork);
+            theta[i] = num / den;
+        }
+    }
     cudaEventRecord(e1, st);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
     float ms_ = 0.f;
@@ -419,16 +429,16 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         P.mps.sites[k] = newsite;
         P.mps.center = k + 1;
         for (int m = k; m <= K; ++m)
-            if (P.left[m]) { P.free(P.left[m]->d, P.left[m]->n); P.left[m].reset(); }
+            free_block(P, P.left[m]);
         for (int m = 0; m <= k - 1; ++m)
-            if (P.right[m]) { P.free(P.right[m]->d, P.right[m]->n); P.right[m].reset(); }
+            free_block(P, P.right[m]);
     } else {
         P.mps.sites[k + 1] = newsite;
         P.mps.center = k - 1;
         for (int m = 0; m <= k; ++m)
-            if (P.right[m]) { P.free(P.right[m]->d, P.right[m]->n); P.right[m].reset(); }
+            free_block(P, P.right[m]);
         for (int m = k + 1; m <= K; ++m)
-            if (P.left[m]) { P.free(P.left[m]->d, P.left[m]->n); P.left[m].reset(); }
+            free_block(P, P.left[m]);
     }
     // guess for the next bond: U^T Psi A[k+2] (forward) or A[k-1] Psi V (backward)
     const int kn = forward ? k + 1 : k - 1;
@@ -563,7 +573,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         for (auto& b : br) maxd = std::max(maxd, b[2]);
         ensure_ident(P, maxd);
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), 1 << 14);
-        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1) * nr);
+        ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1) * nr);
         pl.upload(st);
         DMRG_CHECK_CUDA(cudaMemsetAsync(next_psi, 0, (size_t)nr * ndim * 8, st));
         BufTable b2{};
