@@ -1,0 +1,22 @@
+// Block Jacobi symmetric eigensolver for the reduced density matrices of the
+// decimation step (Sec. 2.1): many CTAs per matrix, all matrices of a
+// decimation in one batch.
+#pragma once
+
+#include <functional>
+#include <vector>
+
+#include "engine.h"
+
+namespace dmrg {
+
+// Diagonalises every job's A (n x n, row-major, leading dimension lda; read
+// only): eigenvalues to w[n], eigenvectors to the columns of V (ld lda).
+// Works on private padded copies allocated through alloc_f / free_f
+// (element counts).  Stops when every matrix has off(A)/|A| <= tol or after
+// max_sweeps sweeps; returns the number of sweeps run.
+int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double tol, cudaStream_t st,
+                      const std::function<double*(int64_t)>& alloc_f,
+                      const std::function<void(double*, int64_t)>& free_f);
+
+}  // namespace dmrg

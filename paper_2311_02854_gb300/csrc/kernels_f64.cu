@@ -371,7 +371,6 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_eigh_kernel(const EigJob* 
     double* sn = sm + np;       // np
     int* pp = (int*)(sm + 2 * np);
     int* qq = pp + np;
-    __shared__ double red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
         int i = (int)(idx / n), j = (int)(idx % n);
@@ -382,21 +381,12 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_eigh_kernel(const EigJob* 
         if (tid == 0 && n == 1) J.w[0] = A[0];
         return;
     }
+    // threshold Jacobi: a pair is rotated only if |a_pq| > eps * sqrt(|a_pp a_qq|)
+    // (relative accuracy of small eigenvalues); stop after a sweep without rotations
+    __shared__ int rotated;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int64_t idx = tid; idx < (int64_t)n * n; idx += nt) {
-            int i = (int)(idx / n), j = (int)(idx % n);
-            double x = A[(int64_t)i * lda + j];
-            if (i == j) dia += x * x;
-            else off += x * x;
-        }
-        double offs = block_sum(off, red);
+        if (tid == 0) rotated = 0;
         __syncthreads();
-        double dias = block_sum(dia, red);
-        __shared__ double flag;
-        if (tid == 0) flag = (offs <= 1e-30 * (offs + dias) || offs == 0.0) ? 1.0 : 0.0;
-        __syncthreads();
-        if (flag != 0.0) break;
         for (int r = 0; r < ne - 1; ++r) {
             for (int t = tid; t < np; t += nt) {
                 int a, b;
@@ -410,13 +400,14 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_eigh_kernel(const EigJob* 
                 int p = a < b ? a : b, q = a < b ? b : a;
                 double c = 1.0, s = 0.0;
                 if (q < n) {
-                    double apq = A[(int64_t)p * lda + q];
-                    if (apq != 0.0) {
-                        double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
+                    const double apq = A[(int64_t)p * lda + q];
+                    const double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
+                    if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-300) {
                         double tau = (aqq - app) / (2.0 * apq);
                         double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + tt * tt);
                         s = tt * c;
+                        rotated = 1;
                     }
                 }
                 cs[t] = c;
@@ -456,6 +447,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_eigh_kernel(const EigJob* 
             }
             __syncthreads();
         }
+        if (!rotated) break;
+        __syncthreads();
     }
     for (int i = tid; i < n; i += nt) J.w[i] = A[(int64_t)i * lda + i];
 }

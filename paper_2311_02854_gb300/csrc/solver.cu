@@ -7,6 +7,7 @@
 #include <numeric>
 
 #include "bond.h"
+#include "eig.h"
 
 namespace dmrg {
 
@@ -342,17 +343,14 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         j.lda = g.n;
         woff += g.n;
         jobs.push_back(j);
-        DMRG_REQUIRE(g.n <= 4096, DMRG_EINVAL, "density-matrix sector larger than 4096");
+        DMRG_REQUIRE(g.n <= 16384, DMRG_EINVAL, "density-matrix sector larger than 16384");
     }
-    EigJob* d_jobs = nullptr;
-    DMRG_CHECK_CUDA(cudaMalloc(&d_jobs, jobs.size() * sizeof(EigJob)));
-    DMRG_CHECK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(EigJob), cudaMemcpyHostToDevice, st));
-    dev_jacobi_eigh_batched(d_jobs, (int)jobs.size(), 60, st);
+    block_jacobi_eigh(
+        jobs, 40, 1e-14, st, [&](int64_t n) { return P.alloc(n); }, [&](double* p, int64_t n) { P.free(p, n); });
     std::vector<double> hw(woff), hv(rho_tot);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hw.data(), d_w, woff * 8, cudaMemcpyDeviceToHost, st));
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hv.data(), d_vec, rho_tot * 8, cudaMemcpyDeviceToHost, st));
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d_jobs);
     wl.release();
     P.free(d_rho, 2 * rho_tot + rho_tot + 64);
     // choose the kept states: largest weights, ties by group order then rank
