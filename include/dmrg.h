@@ -84,6 +84,10 @@ typedef struct {
     int64_t scratch_bytes;  /* sigma GEMM scratch per chunk (0 => automatic) */
     int keep_envs;          /* 1: keep every bond's environment (sweeps) */
     int verbose;            /* 0 silent, 1 per-bond lines on stderr */
+    int64_t tc_kchunk;      /* mixed modes: K-depth a sigma output tile accumulates in
+                               FP32 tensor memory before it is added into the FP64
+                               result (0 => default 1024); shorter chains cost more
+                               FP64 atomics and lose less to FP32 accumulation */
 } dmrg_options;
 
 typedef struct {

@@ -17,7 +17,12 @@ namespace {
 enum : int8_t { BUF_L = 0, BUF_R = 1, BUF_INT = 2, BUF_PSI = 3, BUF_SCR = 4, BUF_ID = 5, BUF_OUT = 6, BUF_W = 7 };
 
 constexpr int64_t kChunkF64 = 1 << 14;  // K-depth per accumulation pass (FP64 engine)
-constexpr int64_t kChunkTC = 1 << 15;   // K-depth per accumulation pass (tensor cores)
+// Tensor cores: K-depth one output tile accumulates in FP32 tensor memory
+// before it is added (atomically) into the wider result.  The error of a chain
+// grows linearly with its depth (about 6e-6 relative at 1024 on sigma-like
+// sums), so chains are kept short.
+constexpr int64_t kChunkTC = 1024;       // renormalisation and intermediates (FP32 result)
+constexpr int64_t kChunkSigmaTC = 1024;  // sigma (FP64 result)
 
 struct OpLookup {
     bool ok = false;
@@ -208,7 +213,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
         s.a_buf = BUF_W;
         s.b_buf = (uint8_t)IF.owner;  // BUF_L or BUF_R
         s.alpha = 1.0;
-        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_STORE_SPLIT, 0, 128, 1.0f);
+        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_ATOMIC_F32, kChunkTC, 128, 1.0f);
         else wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TILE_STORE);
         woff += (int64_t)nr * ldw;
     }
@@ -230,8 +235,9 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
             P.w_lo = P.alloc_bf16(wn);
         }
         dev_split_f64(P.d_wcoef, 1, (int)wn, wn, P.w_hi, P.w_lo, wn, P.stream);
-        DMRG_CHECK_CUDA(cudaMemsetAsync(S.h, 0, S.n * 2, P.stream));
-        DMRG_CHECK_CUDA(cudaMemsetAsync(S.l, 0, S.n * 2, P.stream));
+        // FP32 sum of the K-chunks, then split into the bf16 pieces
+        float* acc = alloc_f32(P, S.n);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, S.n * 4, P.stream));
         TcBufs tb = tc_base(P);
         for (int o = 0; o < 2; ++o)
             if (blocks[o]) {
@@ -240,10 +246,12 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
             }
         tb.hi[BUF_W] = P.w_hi;
         tb.lo[BUF_W] = P.w_lo;
-        tb.out[BUF_INT] = S.h;
-        tb.out_lo[BUF_INT] = S.l;
+        tb.out[BUF_INT] = acc;
         launch_seg_gemm_tc(wl, tb, 1, P.nsplit, P.stream);
         P.check_device_error();
+        dev_split_f32(acc, S.n, S.h, S.l, P.stream);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+        free_f32(P, acc, S.n);
     } else {
         BufTable bt{};
         bt.p[BUF_L] = blocks[0] ? blocks[0]->d : nullptr;
@@ -667,7 +675,8 @@ void set_bond(Plan& P, int k) {
             c.Q.off = s.poff;
             c.Q.ld = (int)round_up(s.dr, 8);
         }
-        tl.lower_tc(BUF_SCR, BUF_ID, P.id_n, scratch_cap(P), kChunkTC, TC_ATOMIC_F64);
+        tl.lower_tc(BUF_SCR, BUF_ID, P.id_n, scratch_cap(P), P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : kChunkSigmaTC,
+                    TC_ATOMIC_F64);
         tl.cs.clear();
         ensure_scratch(P, std::max<int64_t>(tl.scratch_elems, 8));
         tl.upload(P.stream);

@@ -81,7 +81,7 @@ dmrg_status grouped_gemm_tc(int nsplit, int n_out, const int* m, const int* n, c
             if (br > 0 && bc > 0) eb = std::max<int64_t>(eb, g.b_off + (br - 1) * g.ldb + bc);
             segs.push_back(g);
         }
-        wl.add_block(c_off[o], 2, m[o], n[o], n[o], segs, TC_ATOMIC_F64, 0, 128, tile_alpha);
+        wl.add_block(c_off[o], 2, m[o], n[o], n[o], segs, TC_ATOMIC_F64, 1024, 128, tile_alpha);
     }
     const int64_t ea_n = ea, eb_n = eb;  // elements actually present in a / b
     ea = round_up(ea, 8);
@@ -145,6 +145,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->scratch_bytes = 0;
     o->keep_envs = 0;
     o->verbose = 0;
+    o->tc_kchunk = 0;
 }
 
 const char* dmrg_version(void) {
