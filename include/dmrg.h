@@ -223,6 +223,42 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
                               const double* alpha, const double* a, const double* b, double* c,
                               void* stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant of dmrg_grouped_gemm with precision DMRG_FP64.
+ * The paper has no counterpart: this exists for callers that cannot obtain
+ * device memory when they need the product (a process whose memory is all
+ * held by its own pool, or one that must not pay the device-wide
+ * synchronisation of cudaFree between overlapped streams).
+ *
+ * Arguments, layouts and results are those of dmrg_grouped_gemm (FP64): C
+ * is overwritten block by block (blocks with no segment are set to zero), so
+ * nothing has to start at zero.  a, b, c are caller-owned device FP64
+ * buffers; the host arrays are read before the call returns.
+ *
+ * The work list (48 bytes per 64 x 64 output tile plus 40 per segment,
+ * tile list padded to 256 bytes) is copied into a fixed static device array
+ * of dmrg_noalloc_scratch_bytes() bytes (4 MiB); larger lists are rejected
+ * with DMRG_EINVAL and a message giving the size needed.  No device memory is
+ * allocated or freed.
+ *
+ * The call is asynchronous on `stream` (launch errors are returned; faults
+ * surface at the caller's next synchronisation).  The first call on a device
+ * looks up the array's device address with that device current (with lazy
+ * module loading the driver also places the array in device memory at that
+ * point); make it before any stream capture begins.  All calls share the one array: calls on
+ * one stream are ordered, but calls whose executions overlap (different
+ * streams, or threads without ordering) race on it and must be serialised by
+ * the caller.
+ * ------------------------------------------------------------------------ */
+dmrg_status dmrg_grouped_gemm_noalloc(int n_out, const int* m, const int* n, const int64_t* c_off,
+                                      const int* seg_beg, const int* k, const int64_t* a_off,
+                                      const int* lda, const int* a_tr, const int64_t* b_off,
+                                      const int* ldb, const int* b_tr, const double* alpha,
+                                      const double* a, const double* b, double* c, void* stream);
+
+/* Size in bytes of the static work-list array of dmrg_grouped_gemm_noalloc. */
+int64_t dmrg_noalloc_scratch_bytes(void);
+
 /* Library build / device information: writes a short string. */
 const char* dmrg_version(void);
 

@@ -71,6 +71,9 @@ _SIGS = {
     "dmrg_destroy": (None, [_P]),
     "dmrg_grouped_gemm": (C.c_int, [C.c_int, C.c_int, _I, _I, _L, _I, _I, _L, _I, _I, _L, _I, _I, _D,
                                     _P, _P, _P, _P]),
+    "dmrg_grouped_gemm_noalloc": (C.c_int, [C.c_int, _I, _I, _L, _I, _I, _L, _I, _I, _L, _I, _I, _D,
+                                            _P, _P, _P, _P]),
+    "dmrg_noalloc_scratch_bytes": (C.c_int64, []),
 }
 
 
@@ -256,3 +259,35 @@ def grouped_gemm(precision, blocks, a, b, c, stream=None):
     code = lib().dmrg_grouped_gemm(int(precision), len(ms), *ptrs, alpha.ctypes.data_as(_D), _ptr(a), _ptr(b),
                                    _ptr(c), _stream(stream))
     _check(code, None)
+
+
+def grouped_gemm_noalloc(blocks, a, b, c, stream=None):
+    """dmrg_grouped_gemm_noalloc: the FP64 grouped GEMM with its work list in a
+    static device array, so the call allocates no device memory.  ``blocks`` as
+    for grouped_gemm."""
+    ms, ns, coff, beg = [], [], [], [0]
+    k, ao, la, at, bo, lb, bt, al = [], [], [], [], [], [], [], []
+    for (m, n, co, segs) in blocks:
+        ms.append(m)
+        ns.append(n)
+        coff.append(co)
+        for s in segs:
+            k.append(s[0]); ao.append(s[1]); la.append(s[2]); at.append(s[3])
+            bo.append(s[4]); lb.append(s[5]); bt.append(s[6]); al.append(s[7])
+        beg.append(len(k))
+    arrs = [np.ascontiguousarray(ms, dtype=np.int32), np.ascontiguousarray(ns, dtype=np.int32),
+            np.ascontiguousarray(coff, dtype=np.int64), np.ascontiguousarray(beg, dtype=np.int32),
+            np.ascontiguousarray(k, dtype=np.int32), np.ascontiguousarray(ao, dtype=np.int64),
+            np.ascontiguousarray(la, dtype=np.int32), np.ascontiguousarray(at, dtype=np.int32),
+            np.ascontiguousarray(bo, dtype=np.int64), np.ascontiguousarray(lb, dtype=np.int32),
+            np.ascontiguousarray(bt, dtype=np.int32)]
+    alpha = np.ascontiguousarray(al, dtype=np.float64)
+    ptrs = [x.ctypes.data_as(_L if x.dtype == np.int64 else _I) for x in arrs]
+    code = lib().dmrg_grouped_gemm_noalloc(len(ms), *ptrs, alpha.ctypes.data_as(_D), _ptr(a), _ptr(b), _ptr(c),
+                                           _stream(stream))
+    _check(code, None)
+
+
+def noalloc_scratch_bytes():
+    """Size of the static work-list array of grouped_gemm_noalloc."""
+    return int(lib().dmrg_noalloc_scratch_bytes())

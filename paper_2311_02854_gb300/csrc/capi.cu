@@ -448,4 +448,40 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
     }
 }
 
+dmrg_status dmrg_grouped_gemm_noalloc(int n_out, const int* m, const int* n, const int64_t* c_off, const int* seg_beg,
+                                      const int* k, const int64_t* a_off, const int* lda, const int* a_tr,
+                                      const int64_t* b_off, const int* ldb, const int* b_tr, const double* alpha,
+                                      const double* a, const double* b, double* c, void* stream) {
+    if (n_out < 0 || !m || !n || !c_off || !seg_beg || !a || !b || !c) return fail(nullptr, DMRG_EINVAL, "bad arguments");
+    try {
+        WorkList wl;
+        for (int o = 0; o < n_out; ++o) {
+            if (m[o] < 0 || n[o] < 0 || c_off[o] < 0) return fail(nullptr, DMRG_EINVAL, "bad block size");
+            std::vector<Seg> segs;
+            for (int s = seg_beg[o]; s < seg_beg[o + 1]; ++s) {
+                Seg g{};
+                g.a_off = a_off[s];
+                g.b_off = b_off[s];
+                g.k = k[s];
+                g.lda = lda[s];
+                g.ldb = ldb[s];
+                g.a_tr = (uint8_t)(a_tr[s] != 0);
+                g.b_tr = (uint8_t)(b_tr[s] != 0);
+                g.a_buf = 0;
+                g.b_buf = 1;
+                g.alpha = alpha[s];
+                if (g.k < 0 || g.lda < 1 || g.ldb < 1) return fail(nullptr, DMRG_EINVAL, "bad segment");
+                segs.push_back(g);
+            }
+            wl.add_block(c_off[o], 2, m[o], n[o], n[o], segs, TILE_STORE);
+        }
+        grouped_gemm_f64_noalloc(wl, a, b, c, (cudaStream_t)stream);
+        return DMRG_OK;
+    } catch (const Error& e) {
+        return fail(nullptr, e.code, e.what());
+    }
+}
+
+int64_t dmrg_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
+
 }  // extern "C"

@@ -67,6 +67,13 @@ struct WorkList {
 };
 
 void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaStream_t st);
+// FP64 grouped GEMM with the work list in a static device array (noalloc.cu);
+// a, b, c as buffers 0, 1, 2 of the work list
+void grouped_gemm_f64_noalloc(const WorkList& host_wl, const double* a, const double* b, double* c, cudaStream_t st);
+int64_t noalloc_scratch_bytes();
+// the same kernel on device tile / segment lists owned by the caller (one vector)
+void launch_seg_gemm_f64_lists(const Tile* d_tiles, int64_t ntiles, const Seg* d_segs, const BufTable& bt,
+                               cudaStream_t st);
 
 // --- small FP64 kernels (Davidson / decimation) ---------------------------
 // out[i] = sum_k X[i*ldx + k] * y[k], i < m   (deterministic two-pass)

@@ -210,6 +210,15 @@ void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaSt
     DMRG_CHECK_CUDA(cudaGetLastError());
 }
 
+void launch_seg_gemm_f64_lists(const Tile* d_tiles, int64_t ntiles, const Seg* d_segs, const BufTable& bt,
+                               cudaStream_t st) {
+    if (ntiles <= 0) return;
+    DMRG_REQUIRE(ntiles <= 2147483647LL, DMRG_EINVAL, "work list too large for one launch");
+    seg_gemm_f64_kernel<<<dim3((unsigned)ntiles, 1), NT, 0, st>>>(d_tiles, d_segs, bt);
+    ++launch_counter();
+    DMRG_CHECK_CUDA(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // Vector kernels
 // ---------------------------------------------------------------------------
