@@ -106,6 +106,9 @@ typedef struct {
     int64_t precond_fallbacks;    /* MLP -> Jacobi fallbacks */
     int davidson_iters_last;
     double ms_host_plan;          /* host time spent building work lists (all calls) */
+    int64_t sigma_tiles[2];       /* mixed sigma: 128 x 128 output tiles of phase 1 / phase 2 */
+    int64_t sigma_stages[2];      /* mixed sigma: 64-deep K stages of phase 1 / phase 2 */
+    double sigma_mma_flops;       /* mixed sigma: tensor work of the tiles (one bf16 product) */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

@@ -36,10 +36,15 @@ class Stats(C.Structure):
                 ("n_terms", C.c_int64), ("n_items", C.c_int64), ("store_bytes", C.c_int64),
                 ("interm_bytes", C.c_int64), ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("precond_fallbacks", C.c_int64), ("davidson_iters_last", C.c_int),
-                ("ms_host_plan", C.c_double)]
+                ("ms_host_plan", C.c_double), ("sigma_tiles", C.c_int64 * 2), ("sigma_stages", C.c_int64 * 2),
+                ("sigma_mma_flops", C.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            d[f] = list(v) if isinstance(v, C.Array) else v
+        return d
 
 
 def lib_path():

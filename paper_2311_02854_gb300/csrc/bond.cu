@@ -678,6 +678,19 @@ void set_bond(Plan& P, int k) {
         tl.lower_tc(BUF_SCR, BUF_ID, P.id_n, scratch_cap(P), P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : kChunkSigmaTC,
                     TC_ATOMIC_F64);
         tl.cs.clear();
+        for (int ph = 0; ph < 2; ++ph) P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
+        P.stats.sigma_mma_flops = 0.0;
+        for (const auto& ch : tl.chunks)
+            for (int ph = 0; ph < 2; ++ph) {
+                const WorkList& w = ph ? ch.second : ch.first;
+                P.stats.sigma_tiles[ph] += (int64_t)w.tiles.size();
+                for (const Tile& t : w.tiles) {
+                    int64_t kk = 0;
+                    for (int q = t.seg_beg; q < t.seg_end; ++q) kk += round_up(w.segs[q].k, 16);
+                    for (int q = t.seg_beg; q < t.seg_end; ++q) P.stats.sigma_stages[ph] += (w.segs[q].k + 63) / 64;
+                    P.stats.sigma_mma_flops += 2.0 * 128 * 128 * (double)kk;
+                }
+            }
         ensure_scratch(P, std::max<int64_t>(tl.scratch_elems, 8));
         tl.upload(P.stream);
         P.stats.sigma_flops = tl.flops;

@@ -1,10 +1,10 @@
 // Tensor-core segmented grouped GEMM for sm_103a (5th-generation tensor cores):
 // operands staged in shared memory (128B-swizzled canonical layouts, K-major
 // or MN-major), tcgen05.mma kind::f16 with bf16 inputs and FP32 accumulation
-// in tensor memory, completion tracked by mbarriers, persistent CTAs pulling
-// tiles from a counter.  One output tile (128 x 128) accumulates the whole
-// list of K-segments of its block (the term sum of Eq. sigmablk happens in
-// the accumulator).  bf16 "pieces": an operand x is held as hi + lo; with
+// in tensor memory, completion tracked by mbarriers, persistent
+// warp-specialised CTAs (one per SM) walking the tiles round-robin.  One output
+// tile (128 x 128) accumulates the K-segments of its block (the term sum of
+// the sigma reduction happens in the accumulator).  bf16 "pieces": an operand x is held as hi + lo; with
 // nsplit = 2 each product runs as hi*hi + hi*lo + lo*hi.
 #include <cuda_bf16.h>
 
@@ -15,17 +15,10 @@
 namespace dmrg {
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64, THREADS = 128;
+constexpr int TM = 128, TN = 128, TK = 64;
 constexpr int PIECE_BYTES = TM * TK * 2;  // one 128 x 64 bf16 operand tile
 constexpr uint32_t TMEM_COLS = 128;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded waits: 2 s
-
-template <int NSPLIT>
-struct Cfg {
-    static constexpr int STAGES = (NSPLIT == 1) ? 4 : 3;
-    static constexpr int STAGE_BYTES = 2 * NSPLIT * PIECE_BYTES;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -34,7 +27,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int by
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
@@ -109,206 +101,290 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
-// Stage one 128 x 64 tile of an operand into shared memory.
-// Element (r, k) of the operand lives at base[r*ld + k] (mn = 0: K-major) or
-// base[k*ld + r] (mn = 1: MN-major); valid for r < R, k < K (zero-filled outside).
-__device__ __forceinline__ void load_tile(uint32_t sdst, const __nv_bfloat16* base, int ld, int mn, int r0, int R,
-                                          int k0, int K, int tid) {
+// Stage one 128 x 64 (M x K) operand piece into shared memory in the 128B-swizzled
+// canonical layout the MMA descriptors describe.  Element (r, k) of the
+// operand is base[r*ld + k] (mn = 0: K-major) or base[k*ld + r] (mn = 1:
+// MN-major), valid for r < R, k < K; chunks outside are zero-filled (no global
+// read).  Producer thread p always handles the same 16-byte column chunk of 8
+// rows 16 (K-major) or 8 (MN-major) apart, so the swizzle and the validity of
+// the chunk's columns are loop invariant and each copy costs a few instructions.
+__device__ __forceinline__ void load_piece(uint32_t sdst, const __nv_bfloat16* base, int ld, int mn, int r0, int R,
+                                           int k0, int K, int p) {
     if (!mn) {
+        const int c = p & 7, rr = p >> 3;  // chunk, first row (0..15)
+        const int kk = k0 + c * 8;
+        const int cvalid = kk < K ? min(8, K - kk) * 2 : 0;
+        uint32_t dst = sdst + (uint32_t)((rr >> 3) * 1024 + (rr & 7) * 128 + ((c ^ (rr & 7)) << 4));
+        const __nv_bfloat16* src = base + (int64_t)(r0 + rr) * ld + kk;
+        const int64_t step = (int64_t)16 * ld;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int idx = tid + i * THREADS;
-            const int r = idx >> 3, c = idx & 7;
-            const int kk = k0 + c * 8;
-            int valid = 0;
-            const __nv_bfloat16* src = base;
-            if (r0 + r < R && kk < K) {
-                valid = min(8, K - kk);
-                src = base + (int64_t)(r0 + r) * ld + kk;
-            }
-            const uint32_t dst = sdst + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
-            cp_async16(dst, src, valid * 2);
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = (r0 + rr + 16 * j < R) && cvalid > 0;
+            cp_async16(dst, ok ? (const void*)src : (const void*)base, ok ? cvalid : 0);
+            dst += 2048;
+            src += step;
         }
     } else {
+        const int c = p & 15, kr = p >> 4;  // chunk along M, first K row (0..7)
+        const int rr = r0 + c * 8;
+        const int cvalid = rr < R ? min(8, R - rr) * 2 : 0;
+        uint32_t dst = sdst + (uint32_t)((c >> 3) * 1024 + kr * 128 + (((c & 7) ^ kr) << 4));
+        const __nv_bfloat16* src = base + (int64_t)(k0 + kr) * ld + rr;
+        const int64_t step = (int64_t)8 * ld;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int idx = tid + i * THREADS;
-            const int kr = idx >> 4, c = idx & 15;
-            const int rr = r0 + c * 8;
-            int valid = 0;
-            const __nv_bfloat16* src = base;
-            if (k0 + kr < K && rr < R) {
-                valid = min(8, R - rr);
-                src = base + (int64_t)(k0 + kr) * ld + rr;
-            }
-            const uint32_t dst =
-                sdst + (uint32_t)((((kr >> 3) * 2 + (c >> 3)) * 1024) + (kr & 7) * 128 + (((c & 7) ^ (kr & 7)) << 4));
-            cp_async16(dst, src, valid * 2);
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = (k0 + kr + 8 * j < K) && cvalid > 0;
+            cp_async16(dst, ok ? (const void*)src : (const void*)base, ok ? cvalid : 0);
+            dst += 2048;
+            src += step;
         }
     }
 }
 
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+    // wait until at most n committed groups are pending (n is 0..2 here)
+    if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
+
+// Roles of the persistent kernel (one CTA per SM):
+//   warps 0-3  epilogue: TMEM -> registers -> global (warp w owns TMEM lanes 32w..32w+31)
+//   warps 4-7  producers: cp.async of the operand pieces of each 64-deep K stage
+//   warp  8    MMA issuer (lane 0): tcgen05.mma into one of two TMEM accumulators
+// Stages flow through a ring of STAGES shared-memory slots (full / empty
+// mbarriers); tiles alternate between two 128-column TMEM accumulators
+// (tmem_full / tmem_empty), so loads of the next stages, the MMAs of one tile
+// and the epilogue of the previous tile overlap.  Every wait is bounded; on a
+// timeout the CTA sets the error word and winds down.
+constexpr int kEpiWarps = 4, kProdWarps = 4;
+constexpr int NPROD = kProdWarps * 32;
+constexpr int THREADS2 = (kEpiWarps + kProdWarps + 1) * 32;
+constexpr int LAG = 2;  // producer arrives on a stage's full barrier LAG stages after issuing it
+
 template <int NSPLIT>
-__global__ void __launch_bounds__(THREADS, 1)
+struct Cfg2 {
+    static constexpr int STAGES = (NSPLIT == 1) ? 6 : 3;
+    static constexpr int STAGE_BYTES = 2 * NSPLIT * PIECE_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
+
+struct StageMeta {
+    uint8_t a_mn, b_mn, neg, flags;  // flags: 1 first stage of a tile, 2 last, 4 no MMA (empty tile)
+    int32_t k16;                     // 16-deep MMA steps holding data (1..4)
+};
+
+__device__ __forceinline__ int tile_stages(const Tile& T, const Seg* __restrict__ segs) {
+    int nst = 0;
+    for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + TK - 1) / TK;
+    return nst;
+}
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(THREADS2, 1)
     tc_seg_gemm_kernel(const Tile* __restrict__ tiles, int ntiles, int nvec, const Seg* __restrict__ segs, TcBufs B) {
-    using C = Cfg<NSPLIT>;
+    using C = Cfg2<NSPLIT>;
+    constexpr int S = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[C::STAGES];
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ StageMeta meta[S];
     __shared__ uint32_t tmem_base_s;
-    __shared__ int tile_s;
-    __shared__ int stage_mn[C::STAGES][3];  // a_mn, b_mn, neg of the stage held in a slot
+    __shared__ int fail_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base_s)),
-                     "r"(TMEM_COLS)
+                     "r"(2 * TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < C::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), NPROD);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull_bar[b]), 1);
+            mbar_init(smem_u32(&tempty_bar[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        fail_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_s;
-
     const int total = ntiles * nvec;
-    uint32_t g = 0;  // stages issued by this CTA (slot = g % STAGES)
     bool failed = false;
-    for (;;) {
-        if (tid == 0) tile_s = atomicAdd(B.counter, 1);
-        __syncthreads();
-        const int idx = tile_s;
-        if (idx >= total) break;
-        const int tix = idx % ntiles, v = idx / ntiles;
-        const Tile T = tiles[tix];
-        int nst = 0;
-        for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + TK - 1) / TK;
 
-        if (nst > 0) {
-            int ls = T.seg_beg, lk = 0;  // load cursor
-            while (ls < T.seg_end && lk >= segs[ls].k) { ++ls; lk = 0; }
-            int ms = ls, mk = 0;         // mma cursor
-            auto issue_load = [&](uint32_t q) -> bool {
-                const uint32_t slot = q % C::STAGES;
-                if (q >= (uint32_t)C::STAGES) {
-                    if (!mbar_wait(smem_u32(&bars[slot]), ((q - C::STAGES) / C::STAGES) & 1u)) return false;
-                }
-                const Seg S = segs[ls];
-                const int a_mn = S.a_tr ? 1 : 0;
-                const int b_mn = S.b_tr ? 0 : 1;
-                const uint32_t sa = sbase + slot * C::STAGE_BYTES;
-                const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
-                const int64_t ao = S.a_off + (int64_t)v * B.vstride[S.a_buf];
-                const int64_t bo = S.b_off + (int64_t)v * B.vstride[S.b_buf];
-                load_tile(sa, B.hi[S.a_buf] + ao, S.lda, a_mn, T.m0, T.m, lk, S.k, tid);
-                load_tile(sb, B.hi[S.b_buf] + bo, S.ldb, b_mn, T.n0, T.n, lk, S.k, tid);
-                if (NSPLIT == 2) {
-                    load_tile(sa + PIECE_BYTES, B.lo[S.a_buf] + ao, S.lda, a_mn, T.m0, T.m, lk, S.k, tid);
-                    load_tile(sb + PIECE_BYTES, B.lo[S.b_buf] + bo, S.ldb, b_mn, T.n0, T.n, lk, S.k, tid);
-                }
-                if (tid == 0) {
-                    stage_mn[slot][0] = a_mn;
-                    stage_mn[slot][1] = b_mn;
-                    stage_mn[slot][2] = S.alpha < 0.0 ? 1 : 0;
-                }
-                cp_async_commit();
-                lk += TK;
-                while (ls < T.seg_end && lk >= segs[ls].k) { ++ls; lk = 0; }
-                return true;
-            };
-            bool ok = issue_load(g);
-            for (int t = 0; t < nst && ok; ++t) {
-                if (t + 1 < nst) {
-                    ok = issue_load(g + t + 1);
-                    cp_async_wait1();
-                } else {
-                    cp_async_wait0();
-                }
-                fence_proxy_async();
-                if (__syncthreads_or(!ok)) {
-                    ok = false;
-                    break;
-                }
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint32_t slot = (g + t) % C::STAGES;
-                    const uint32_t sa = sbase + slot * C::STAGE_BYTES;
+    if (warp >= kEpiWarps && warp < kEpiWarps + kProdWarps) {
+        // ---------------- producers ----------------
+        const int p = tid - kEpiWarps * 32;
+        uint32_t q = 0;
+        auto finish_stage = [&](uint32_t qs) {  // stage qs's copies are complete: publish it
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&full_bar[qs % S]));
+        };
+        auto begin_stage = [&](uint32_t qs) -> bool {  // wait until slot of stage qs is free
+            if (qs >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[qs % S]), ((qs / S) - 1) & 1u)) return false;
+            return true;
+        };
+        auto end_issue = [&]() {  // after committing stage q: publish stage q - LAG
+            cp_async_commit();
+            if (q >= (uint32_t)LAG) {
+                cp_async_wait_n(LAG);
+                finish_stage(q - LAG);
+            }
+            ++q;
+        };
+        for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
+            const int tix = t % ntiles, v = t / ntiles;
+            const Tile T = tiles[tix];
+            const int nst = tile_stages(T, segs);
+            if (nst == 0) {
+                if (!begin_stage(q)) { failed = true; break; }
+                if (p == 0) meta[q % S] = StageMeta{0, 0, 0, 1 | 2 | 4, 0};
+                end_issue();
+                continue;
+            }
+            int done = 0;
+            for (int s = T.seg_beg; s < T.seg_end && !failed; ++s) {
+                const Seg Sg = segs[s];
+                const int a_mn = Sg.a_tr ? 1 : 0, b_mn = Sg.b_tr ? 0 : 1;
+                const int64_t ao = Sg.a_off + (int64_t)v * B.vstride[Sg.a_buf];
+                const int64_t bo = Sg.b_off + (int64_t)v * B.vstride[Sg.b_buf];
+                for (int k0 = 0; k0 < Sg.k; k0 += TK) {
+                    if (!begin_stage(q)) { failed = true; break; }
+                    const uint32_t sa = sbase + (q % S) * C::STAGE_BYTES;
                     const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
-                    const int a_mn = stage_mn[slot][0], b_mn = stage_mn[slot][1], neg = stage_mn[slot][2];
-                    const uint32_t id = idesc(a_mn, b_mn, neg);
+                    load_piece(sa, B.hi[Sg.a_buf] + ao, Sg.lda, a_mn, T.m0, T.m, k0, Sg.k, p);
+                    load_piece(sb, B.hi[Sg.b_buf] + bo, Sg.ldb, b_mn, T.n0, T.n, k0, Sg.k, p);
+                    if (NSPLIT == 2) {
+                        load_piece(sa + PIECE_BYTES, B.lo[Sg.a_buf] + ao, Sg.lda, a_mn, T.m0, T.m, k0, Sg.k, p);
+                        load_piece(sb + PIECE_BYTES, B.lo[Sg.b_buf] + bo, Sg.ldb, b_mn, T.n0, T.n, k0, Sg.k, p);
+                    }
+                    if (p == 0) {
+                        const int kv = min(TK, Sg.k - k0);
+                        meta[q % S] = StageMeta{(uint8_t)a_mn, (uint8_t)b_mn, (uint8_t)(Sg.alpha < 0.0 ? 1 : 0),
+                                                (uint8_t)((done == 0 ? 1 : 0) | (done == nst - 1 ? 2 : 0)),
+                                                (kv + 15) / 16};
+                    }
+                    end_issue();
+                    ++done;
+                }
+            }
+        }
+        // publish the last LAG stages (or wind down after a failure)
+        cp_async_wait0();
+        for (uint32_t qs = (q >= (uint32_t)LAG ? q - LAG : 0); qs < q; ++qs) finish_stage(qs);
+    } else if (warp == kEpiWarps + kProdWarps) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t q = 0, tc = 0;
+            for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
+                const uint32_t buf = tc & 1u, use = tc >> 1;
+                if (use > 0 && !mbar_wait(smem_u32(&tempty_bar[buf]), (use - 1) & 1u)) { failed = true; break; }
+                tc_fence_after();
+                const uint32_t dt = tmem + buf * TMEM_COLS;
+                for (;;) {
+                    const uint32_t slot = q % S;
+                    if (!mbar_wait(smem_u32(&full_bar[slot]), (q / S) & 1u)) { failed = true; break; }
+                    tc_fence_after();
+                    const StageMeta M = meta[slot];
+                    if (!(M.flags & 4)) {
+                        const uint32_t sa = sbase + slot * C::STAGE_BYTES;
+                        const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
+                        const uint32_t id = idesc(M.a_mn, M.b_mn, M.neg);
+                        for (int kk = 0; kk < M.k16; ++kk) {
 #pragma unroll
-                    for (int kk = 0; kk < TK / 16; ++kk) {
-#pragma unroll
-                        for (int p = 0; p < (NSPLIT == 2 ? 3 : 1); ++p) {
-                            const int pa = (p == 2) ? 1 : 0;  // products: hi*hi, hi*lo, lo*hi
-                            const int pb = (p == 1) ? 1 : 0;
-                            const uint32_t a_s = sa + pa * PIECE_BYTES;
-                            const uint32_t b_s = sb + pb * PIECE_BYTES;
-                            const uint64_t ad = a_mn ? sdesc(a_s + kk * 4096, 1024, 2048) : sdesc(a_s + kk * 32, 16, 1024);
-                            const uint64_t bd = b_mn ? sdesc(b_s + kk * 4096, 1024, 2048) : sdesc(b_s + kk * 32, 16, 1024);
-                            const uint32_t acc = (t == 0 && kk == 0 && p == 0) ? 0u : 1u;
-                            mma_bf16(tmem, ad, bd, id, acc);
+                            for (int pr = 0; pr < (NSPLIT == 2 ? 3 : 1); ++pr) {
+                                const int pa = (pr == 2) ? 1 : 0;  // products: hi*hi, hi*lo, lo*hi
+                                const int pb = (pr == 1) ? 1 : 0;
+                                const uint32_t a_s = sa + pa * PIECE_BYTES;
+                                const uint32_t b_s = sb + pb * PIECE_BYTES;
+                                const uint64_t ad =
+                                    M.a_mn ? sdesc(a_s + kk * 4096, 1024, 2048) : sdesc(a_s + kk * 32, 16, 1024);
+                                const uint64_t bd =
+                                    M.b_mn ? sdesc(b_s + kk * 4096, 1024, 2048) : sdesc(b_s + kk * 32, 16, 1024);
+                                const uint32_t acc = ((M.flags & 1) && kk == 0 && pr == 0) ? 0u : 1u;
+                                mma_bf16(dt, ad, bd, id, acc);
+                            }
                         }
                     }
-                    mma_commit(smem_u32(&bars[slot]));
+                    mma_commit(smem_u32(&empty_bar[slot]));
+                    ++q;
+                    if (M.flags & 2) break;
                 }
-                mk += TK;
-                while (ms < T.seg_end && mk >= segs[ms].k) { ++ms; mk = 0; }
+                if (failed) break;
+                mma_commit(smem_u32(&tfull_bar[buf]));
             }
-            if (!ok) {
-                failed = true;
-                g += nst;
-                break;
-            }
-            g += nst;
-            // all MMAs of the tile are complete once the last commit has arrived
-            const uint32_t last = g - 1;
-            const bool done = mbar_wait(smem_u32(&bars[last % C::STAGES]), (last / C::STAGES) & 1u);
-            if (__syncthreads_or(!done)) {
-                failed = true;
-                break;
-            }
-            tc_fence_after();
+            // every MMA issued by this thread has completed once this commit arrives
+            mma_commit(smem_u32(&drain_bar));
+            if (!mbar_wait(smem_u32(&drain_bar), 0)) failed = true;
         }
-
-        // epilogue: TMEM lane = output row (warp w owns rows 32w..32w+31)
-        const int row = warp * 32 + lane;
-        const int r = T.m0 + row;
-        const bool rok = r < T.m;
-        const float alpha = T.alpha;
-        for (int cg = 0; cg < TN / 32; ++cg) {
-            uint32_t acc[32];
+    } else {
+        // ---------------- epilogue ----------------
+        uint32_t tc = 0;
+        for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
+            const uint32_t buf = tc & 1u, use = tc >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[buf]), use & 1u) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform (tcgen05.ld is warp-collective)
+            if (!ok) { failed = true; break; }
+            __syncwarp();
+            tc_fence_after();
+            const int tix = t % ntiles, v = t / ntiles;
+            const Tile T = tiles[tix];
+            const int nst = tile_stages(T, segs);
+            const int row = warp * 32 + lane;
+            const int r = T.m0 + row;
+            const bool rok = r < T.m;
+            const float alpha = T.alpha;
+            uint32_t acc[TN];
             if (nst > 0) {
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), acc);
+#pragma unroll
+                for (int cg = 0; cg < TN / 32; ++cg) {
+                    uint32_t (&a32)[32] = *reinterpret_cast<uint32_t(*)[32]>(&acc[cg * 32]);
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + buf * TMEM_COLS + (uint32_t)(cg * 32), a32);
+                }
                 tmem_wait_ld();
             } else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = 0u;
+                for (int j = 0; j < TN; ++j) acc[j] = 0u;
             }
-            const int c0 = T.n0 + cg * 32;
-            if (!rok || c0 >= T.n) continue;
-            const int ncol = min(32, T.n - c0);
-            const int64_t off = T.c_off + (int64_t)r * T.ldc + c0 + (int64_t)v * B.out_vstride[T.c_buf];
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
+            if (!rok || (nst == 0 && (T.mode == TC_ATOMIC_F64 || T.mode == TC_ATOMIC_F32))) continue;
+            const int ncol = min(TN, T.n - T.n0);
+            const int64_t off = T.c_off + (int64_t)r * T.ldc + T.n0 + (int64_t)v * B.out_vstride[T.c_buf];
             if (T.mode == TC_ATOMIC_F64) {
-                if (nst == 0) continue;
                 double* o = (double*)B.out[T.c_buf] + off;
-                for (int j = 0; j < ncol; ++j) atomicAdd(o + j, (double)alpha * (double)__uint_as_float(acc[j]));
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (j < ncol) atomicAdd(o + j, (double)alpha * (double)__uint_as_float(acc[j]));
             } else if (T.mode == TC_ATOMIC_F32) {
-                if (nst == 0) continue;
                 float* o = (float*)B.out[T.c_buf] + off;
-                for (int j = 0; j < ncol; ++j) atomicAdd(o + j, alpha * __uint_as_float(acc[j]));
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (j < ncol) atomicAdd(o + j, alpha * __uint_as_float(acc[j]));
             } else if (T.mode == TC_STORE_F32) {
                 float* o = (float*)B.out[T.c_buf] + off;
-                for (int j = 0; j < ncol; ++j) o[j] = alpha * __uint_as_float(acc[j]);
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (j < ncol) o[j] = alpha * __uint_as_float(acc[j]);
             } else {  // TC_STORE_SPLIT: chunks of 8 (rows padded to multiples of 8)
                 __nv_bfloat16* oh = (__nv_bfloat16*)B.out[T.c_buf] + off;
                 __nv_bfloat16* ol = (__nv_bfloat16*)B.out_lo[T.c_buf] + off;
-                for (int j0 = 0; j0 < ncol; j0 += 8) {
+#pragma unroll
+                for (int j0 = 0; j0 < TN; j0 += 8) {
+                    if (j0 >= ncol) break;
                     __align__(16) __nv_bfloat16 h8[8], l8[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -322,20 +398,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
         }
-        tc_fence_before();
-        __syncthreads();
     }
-    if (failed && tid == 0) atomicExch(B.err, 1);
-    // make sure no MMA is in flight before releasing tensor memory
-    if (failed && g > 0) {
-        const uint32_t last = g - 1;
-        (void)mbar_wait(smem_u32(&bars[last % C::STAGES]), (last / C::STAGES) & 1u);
+    if (failed) {
+        fail_s = 1;
+        atomicExch(B.err, 1);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * TMEM_COLS)
                      : "memory");
     }
 }
@@ -409,18 +481,18 @@ void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit
         static bool attr = false;
         if (!attr) {
             DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_seg_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Cfg<2>::SMEM));
+                                                 Cfg2<2>::SMEM));
             attr = true;
         }
-        tc_seg_gemm_kernel<2><<<grid, THREADS, Cfg<2>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
+        tc_seg_gemm_kernel<2><<<grid, THREADS2, Cfg2<2>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
     } else {
         static bool attr = false;
         if (!attr) {
             DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_seg_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Cfg<1>::SMEM));
+                                                 Cfg2<1>::SMEM));
             attr = true;
         }
-        tc_seg_gemm_kernel<1><<<grid, THREADS, Cfg<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
+        tc_seg_gemm_kernel<1><<<grid, THREADS2, Cfg2<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
     }
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
