@@ -43,16 +43,22 @@ OpLookup lookup(const BlockLayout& lay, const Interms& im, const OpRef& r, int i
     const Family* f;
     int64_t rowbase;
     int8_t buf;
+    int nrows;
     if (r.src == SRC_STORE) {
         f = &lay.fams[r.fam];
         rowbase = f->base + (int64_t)r.row * f->stride;
         buf = store_buf;
+        nrows = f->nops();
     } else {
         const IntermFamily& IF = im.fams[r.fam];
         f = &lay.fams[IF.src_fam];
         rowbase = IF.base + (int64_t)r.row * f->stride;
         buf = BUF_INT;
+        nrows = (int)IF.rows.size();
     }
+    o.v.z = r.row;
+    o.v.nz = nrows;
+    o.v.zstride = f->stride;
     const Basis& b = lay.basis;
     if (!r.tr) {
         int pr = f->pair_of_ket[i];
@@ -106,6 +112,46 @@ TcBufs tc_base(Plan& P) {
     TcBufs tb{};
     tb.counter = P.d_ctr;
     tb.err = P.d_ctr + 1;
+    return tb;
+}
+
+// bf16 pieces of the padded wavefunction copy for n elements (all vectors of a launch)
+void ensure_psi_pieces(Plan& P, int64_t n) {
+    if (n <= P.n_ppc) return;
+    P.free_bf16(P.ps_hi, P.n_ppc);
+    P.free_bf16(P.ps_lo, P.n_ppc);
+    P.n_ppc = n;
+    P.ps_hi = P.alloc_bf16(n);
+    P.ps_lo = P.alloc_bf16(n);
+}
+
+// Buffers of the mixed sigma at bond k (out: FP64 result of vector 0)
+TcBufs sigma_bufs(Plan& P, int k, double* out) {
+    DMRG_REQUIRE(k >= 1 && k <= P.K - 1 && P.left[k - 1] && P.right[k + 1], DMRG_EINVAL,
+                 "sigma buffers requested without the bond's environments");
+    const Block& L = *P.left[k - 1];
+    const Block& R = *P.right[k + 1];
+    const int64_t per = std::max<int64_t>(P.sigma_tc.scratch_elems, 8);
+    TcBufs tb = tc_base(P);
+    tb.hi[BUF_L] = L.h;
+    tb.lo[BUF_L] = L.l;
+    tb.hi[BUF_R] = R.h;
+    tb.lo[BUF_R] = R.l;
+    tb.hi[BUF_INT] = P.interm.h;
+    tb.lo[BUF_INT] = P.interm.l;
+    tb.hi[BUF_PSI] = P.ps_hi;
+    tb.lo[BUF_PSI] = P.ps_lo;
+    tb.vstride[BUF_PSI] = P.dim_pad;
+    tb.hi[BUF_SCR] = P.s_hi;
+    tb.lo[BUF_SCR] = P.s_lo;
+    tb.vstride[BUF_SCR] = per;
+    tb.hi[BUF_ID] = P.id_hi;
+    tb.lo[BUF_ID] = P.id_lo;
+    tb.out[BUF_OUT] = out;
+    tb.out_vstride[BUF_OUT] = P.dim;
+    tb.out[BUF_SCR] = P.s_hi;
+    tb.out_lo[BUF_SCR] = P.s_lo;
+    tb.out_vstride[BUF_SCR] = per;
     return tb;
 }
 
@@ -675,14 +721,18 @@ void set_bond(Plan& P, int k) {
             c.Q.off = s.poff;
             c.Q.ld = (int)round_up(s.dr, 8);
         }
-        tl.lower_tc(BUF_SCR, BUF_ID, P.id_n, scratch_cap(P), P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : kChunkSigmaTC,
-                    TC_ATOMIC_F64);
+        // vectors per launch (block Davidson passes up to n_roots at once)
+        const int G = std::max(1, P.opt.n_roots);
+        int64_t vs[kMaxBufs] = {};
+        vs[BUF_PSI] = P.dim_pad;
+        tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, std::max<int64_t>(scratch_cap(P) / G, 1 << 20),
+                     P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : kChunkSigmaTC, TC_ATOMIC_F64, vs, G);
         tl.cs.clear();
         for (int ph = 0; ph < 2; ++ph) P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
         P.stats.sigma_mma_flops = 0.0;
-        for (const auto& ch : tl.chunks)
+        for (const auto& ch : tl.tchunks)
             for (int ph = 0; ph < 2; ++ph) {
-                const WorkList& w = ph ? ch.second : ch.first;
+                const TmaWorkList& w = ph ? ch.second : ch.first;
                 P.stats.sigma_tiles[ph] += (int64_t)w.tiles.size();
                 for (const Tile& t : w.tiles) {
                     int64_t kk = 0;
@@ -691,8 +741,13 @@ void set_bond(Plan& P, int k) {
                     P.stats.sigma_mma_flops += 2.0 * 128 * 128 * (double)kk;
                 }
             }
-        ensure_scratch(P, std::max<int64_t>(tl.scratch_elems, 8));
-        tl.upload(P.stream);
+        ensure_scratch(P, (int64_t)G * tl.scratch_elems);
+        ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
+        for (auto& ch : tl.tchunks) {
+            ch.first.upload(P.stream);
+            ch.second.upload(P.stream);
+        }
+        tl.maps.encode_upload(sigma_bufs(P, k, nullptr), P.nsplit, P.stream);
         P.stats.sigma_flops = tl.flops;
         // padded bf16 copy of psi: one split job per sector
         std::vector<SplitJob> jobs;
@@ -837,47 +892,19 @@ void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
         P.stats.sigma_calls += nvec;
         return;
     }
-    // mixed precision: bf16 pieces of psi, tensor-core products, FP64 accumulation of sigma
-    const ProductList& tl = P.sigma_tc;
-    const int64_t per = std::max<int64_t>(tl.scratch_elems, 8);
-    const int group = (int)std::max<int64_t>(1, std::min<int64_t>(nvec, P.n_spc / per));
-    const int64_t need_psi = (int64_t)group * P.dim_pad;
-    if (need_psi > P.n_ppc) {
-        P.free_bf16(P.ps_hi, P.n_ppc);
-        P.free_bf16(P.ps_lo, P.n_ppc);
-        P.n_ppc = need_psi;
-        P.ps_hi = P.alloc_bf16(need_psi);
-        P.ps_lo = P.alloc_bf16(need_psi);
-    }
-    const Block& L = *P.left[P.bond - 1];
-    const Block& R = *P.right[P.bond + 1];
-    for (int v0 = 0; v0 < nvec; v0 += group) {
-        const int nv = std::min(group, nvec - v0);
+    // mixed precision: bf16 pieces of psi, tensor-core products (TMA-staged), FP64 accumulation of sigma
+    ProductList& tl = P.sigma_tc;
+    const int G = std::max(1, P.opt.n_roots);
+    ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
+    for (int v0 = 0; v0 < nvec; v0 += G) {
+        const int nv = std::min(G, nvec - v0);
         for (int v = 0; v < nv; ++v)
             dev_split_blocks(psi + (int64_t)(v0 + v) * P.dim, P.d_psi_jobs, P.n_psi_jobs,
                              P.ps_hi + (int64_t)v * P.dim_pad, P.ps_lo + (int64_t)v * P.dim_pad, st);
         DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v0 * P.dim, 0, (size_t)nv * P.dim * 8, st));
-        TcBufs tb = tc_base(P);
-        tb.hi[BUF_L] = L.h;
-        tb.lo[BUF_L] = L.l;
-        tb.hi[BUF_R] = R.h;
-        tb.lo[BUF_R] = R.l;
-        tb.hi[BUF_INT] = P.interm.h;
-        tb.lo[BUF_INT] = P.interm.l;
-        tb.hi[BUF_PSI] = P.ps_hi;
-        tb.lo[BUF_PSI] = P.ps_lo;
-        tb.vstride[BUF_PSI] = P.dim_pad;
-        tb.hi[BUF_SCR] = P.s_hi;
-        tb.lo[BUF_SCR] = P.s_lo;
-        tb.vstride[BUF_SCR] = per;
-        tb.hi[BUF_ID] = P.id_hi;
-        tb.lo[BUF_ID] = P.id_lo;
-        tb.out[BUF_OUT] = out + (int64_t)v0 * P.dim;
-        tb.out_vstride[BUF_OUT] = P.dim;
-        tb.out[BUF_SCR] = P.s_hi;
-        tb.out_lo[BUF_SCR] = P.s_lo;
-        tb.out_vstride[BUF_SCR] = per;
-        P.sigma_tc.run_tc(tb, nv, P.nsplit, st);
+        const TcBufs tb = sigma_bufs(P, P.bond, out + (int64_t)v0 * P.dim);
+        if (tl.maps.stale(tb)) tl.maps.encode_upload(tb, P.nsplit, st);
+        tl.run_tma(tb, nv, P.nsplit, st);
     }
     P.stats.sigma_calls += nvec;
     P.check_device_error();

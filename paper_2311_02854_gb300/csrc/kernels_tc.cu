@@ -183,6 +183,70 @@ __device__ __forceinline__ int tile_stages(const Tile& T, const Seg* __restrict_
     return nst;
 }
 
+// Epilogue of one tile by warps 0-3 (warp w owns TMEM lanes / tile rows
+// 32w..32w+31): accumulator columns at TMEM address tacc -> registers, release
+// of the accumulator (one arrive per warp on `tempty`), then alpha * acc
+// written or accumulated into the output in the tile's mode.
+template <int NSPLIT>
+__device__ __forceinline__ void epilogue_tile(const Tile& T, int v, int nst, uint32_t tacc, int warp, int lane,
+                                              const TcBufs& B, uint32_t tempty) {
+    const int row = warp * 32 + lane;
+    const int r = T.m0 + row;
+    const bool rok = r < T.m;
+    const float alpha = T.alpha;
+    uint32_t acc[TN];
+    if (nst > 0) {
+#pragma unroll
+        for (int cg = 0; cg < TN / 32; ++cg) {
+            uint32_t (&a32)[32] = *reinterpret_cast<uint32_t(*)[32]>(&acc[cg * 32]);
+            tmem_ld32(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cg * 32), a32);
+        }
+        tmem_wait_ld();
+    } else {
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[j] = 0u;
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(tempty);
+    if (!rok || (nst == 0 && (T.mode == TC_ATOMIC_F64 || T.mode == TC_ATOMIC_F32))) return;
+    const int ncol = min(TN, T.n - T.n0);
+    const int64_t off = T.c_off + (int64_t)r * T.ldc + T.n0 + (int64_t)v * B.out_vstride[T.c_buf];
+    if (T.mode == TC_ATOMIC_F64) {
+        double* o = (double*)B.out[T.c_buf] + off;
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            if (j < ncol) atomicAdd(o + j, (double)alpha * (double)__uint_as_float(acc[j]));
+    } else if (T.mode == TC_ATOMIC_F32) {
+        float* o = (float*)B.out[T.c_buf] + off;
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            if (j < ncol) atomicAdd(o + j, alpha * __uint_as_float(acc[j]));
+    } else if (T.mode == TC_STORE_F32) {
+        float* o = (float*)B.out[T.c_buf] + off;
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+            if (j < ncol) o[j] = alpha * __uint_as_float(acc[j]);
+    } else {  // TC_STORE_SPLIT: chunks of 8 (rows padded to multiples of 8)
+        __nv_bfloat16* oh = (__nv_bfloat16*)B.out[T.c_buf] + off;
+        __nv_bfloat16* ol = (__nv_bfloat16*)B.out_lo[T.c_buf] + off;
+#pragma unroll
+        for (int j0 = 0; j0 < TN; j0 += 8) {
+            if (j0 >= ncol) break;
+            __align__(16) __nv_bfloat16 h8[8], l8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float x = alpha * __uint_as_float(acc[j0 + j]);
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                h8[j] = h;
+                l8[j] = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
+            *(uint4*)(oh + j0) = *(const uint4*)h8;
+            if (NSPLIT == 2) *(uint4*)(ol + j0) = *(const uint4*)l8;
+        }
+    }
+}
+
 template <int NSPLIT>
 __global__ void __launch_bounds__(THREADS2, 1)
     tc_seg_gemm_kernel(const Tile* __restrict__ tiles, int ntiles, int nvec, const Seg* __restrict__ segs, TcBufs B) {
@@ -342,67 +406,231 @@ __global__ void __launch_bounds__(THREADS2, 1)
             const int tix = t % ntiles, v = t / ntiles;
             const Tile T = tiles[tix];
             const int nst = tile_stages(T, segs);
-            const int row = warp * 32 + lane;
-            const int r = T.m0 + row;
-            const bool rok = r < T.m;
-            const float alpha = T.alpha;
-            uint32_t acc[TN];
-            if (nst > 0) {
-#pragma unroll
-                for (int cg = 0; cg < TN / 32; ++cg) {
-                    uint32_t (&a32)[32] = *reinterpret_cast<uint32_t(*)[32]>(&acc[cg * 32]);
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + buf * TMEM_COLS + (uint32_t)(cg * 32), a32);
-                }
-                tmem_wait_ld();
-            } else {
-#pragma unroll
-                for (int j = 0; j < TN; ++j) acc[j] = 0u;
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
-            if (!rok || (nst == 0 && (T.mode == TC_ATOMIC_F64 || T.mode == TC_ATOMIC_F32))) continue;
-            const int ncol = min(TN, T.n - T.n0);
-            const int64_t off = T.c_off + (int64_t)r * T.ldc + T.n0 + (int64_t)v * B.out_vstride[T.c_buf];
-            if (T.mode == TC_ATOMIC_F64) {
-                double* o = (double*)B.out[T.c_buf] + off;
-#pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    if (j < ncol) atomicAdd(o + j, (double)alpha * (double)__uint_as_float(acc[j]));
-            } else if (T.mode == TC_ATOMIC_F32) {
-                float* o = (float*)B.out[T.c_buf] + off;
-#pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    if (j < ncol) atomicAdd(o + j, alpha * __uint_as_float(acc[j]));
-            } else if (T.mode == TC_STORE_F32) {
-                float* o = (float*)B.out[T.c_buf] + off;
-#pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    if (j < ncol) o[j] = alpha * __uint_as_float(acc[j]);
-            } else {  // TC_STORE_SPLIT: chunks of 8 (rows padded to multiples of 8)
-                __nv_bfloat16* oh = (__nv_bfloat16*)B.out[T.c_buf] + off;
-                __nv_bfloat16* ol = (__nv_bfloat16*)B.out_lo[T.c_buf] + off;
-#pragma unroll
-                for (int j0 = 0; j0 < TN; j0 += 8) {
-                    if (j0 >= ncol) break;
-                    __align__(16) __nv_bfloat16 h8[8], l8[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float x = alpha * __uint_as_float(acc[j0 + j]);
-                        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                        h8[j] = h;
-                        l8[j] = __float2bfloat16_rn(x - __bfloat162float(h));
-                    }
-                    *(uint4*)(oh + j0) = *(const uint4*)h8;
-                    if (NSPLIT == 2) *(uint4*)(ol + j0) = *(const uint4*)l8;
-                }
-            }
+            epilogue_tile<NSPLIT>(T, v, nst, tmem + buf * TMEM_COLS, warp, lane, B, smem_u32(&tempty_bar[buf]));
         }
     }
     if (failed) {
         fail_s = 1;
         atomicExch(B.err, 1);
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged kernel
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t addr, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(addr), "r"(bytes) : "memory");
+}
+// 64 x 64 box of a 4-D tensor map into shared memory, completion on an mbarrier
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ int tile_stages_t(const Tile& T, const TSeg* __restrict__ segs) {
+    int nst = 0;
+    for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + TK - 1) / TK;
+    return nst;
+}
+
+// One 128 x 64 operand piece as two 64 x 64 boxes.  K-major (mn = 0): rows
+// r0.. of the map at x = k0; MN-major (mn = 1): columns r0.. of the map at
+// rows k0..  Shared layout: K-major rows at 128 B (8-row groups 1 KB apart);
+// MN-major 64-element M halves 8 KB apart, 8-row K groups 1 KB apart.
+__device__ __forceinline__ void tma_piece(uint32_t dst, const CUtensorMap* map, int mn, int r0, int k0, int z, int w,
+                                          uint32_t bar) {
+    if (!mn) {
+        tma_load4(dst, map, k0, r0, z, w, bar);
+        tma_load4(dst + 8192, map, k0, r0 + 64, z, w, bar);
+    } else {
+        tma_load4(dst, map, r0, k0, z, w, bar);
+        tma_load4(dst + 8192, map, r0 + 64, k0, z, w, bar);
+    }
+}
+
+// Roles: warps 0-3 epilogue (as in tc_seg_gemm_kernel), warp 4 lane 0 TMA
+// producer, warp 5 lane 0 MMA issuer.
+constexpr int THREADS3 = (kEpiWarps + 2) * 32;
+
+template <int NSPLIT>
+struct Cfg3 {
+    static constexpr int STAGES = (NSPLIT == 1) ? 6 : 3;
+    static constexpr int STAGE_BYTES = 2 * NSPLIT * PIECE_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(THREADS3, 1)
+    tc_tma_kernel(const Tile* __restrict__ tiles, int ntiles, int nvec, const TSeg* __restrict__ segs,
+                  const CUtensorMap* __restrict__ maps, TcBufs B) {
+    using C = Cfg3<NSPLIT>;
+    constexpr int S = C::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ StageMeta meta[S];
+    __shared__ uint32_t tmem_base_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(2 * TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull_bar[b]), 1);
+            mbar_init(smem_u32(&tempty_bar[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const int total = ntiles * nvec;
+    bool failed = false;
+
+    if (warp == kEpiWarps) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t q = 0;
+            for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
+                const int tix = t % ntiles, v = t / ntiles;
+                const Tile T = tiles[tix];
+                const int nst = tile_stages_t(T, segs);
+                if (nst == 0) {
+                    if (q >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[q % S]), ((q / S) - 1) & 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    meta[q % S] = StageMeta{0, 0, 0, 1 | 2 | 4, 0};
+                    mbar_arrive(smem_u32(&full_bar[q % S]));
+                    ++q;
+                    continue;
+                }
+                int done = 0;
+                for (int s = T.seg_beg; s < T.seg_end && !failed; ++s) {
+                    const TSeg Sg = segs[s];
+                    const int a_mn = Sg.a_tr ? 1 : 0, b_mn = Sg.b_tr ? 0 : 1;
+                    const int aw = Sg.a_pv ? v : 0, bw = Sg.b_pv ? v : 0;
+                    const CUtensorMap* am = maps + 2 * Sg.a_map;
+                    const CUtensorMap* bm = maps + 2 * Sg.b_map;
+                    for (int k0 = 0; k0 < Sg.k; k0 += TK) {
+                        const uint32_t slot = q % S;
+                        if (q >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[slot]), ((q / S) - 1) & 1u)) {
+                            failed = true;
+                            break;
+                        }
+                        const int kv = min(TK, Sg.k - k0);
+                        meta[slot] = StageMeta{(uint8_t)a_mn, (uint8_t)b_mn, (uint8_t)(Sg.sign < 0.f ? 1 : 0),
+                                               (uint8_t)((done == 0 ? 1 : 0) | (done == nst - 1 ? 2 : 0)),
+                                               (kv + 15) / 16};
+                        const uint32_t bar = smem_u32(&full_bar[slot]);
+                        mbar_arrive_tx(bar, (uint32_t)C::STAGE_BYTES);
+                        const uint32_t sa = sbase + slot * C::STAGE_BYTES;
+                        const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
+#pragma unroll
+                        for (int pc = 0; pc < NSPLIT; ++pc) {
+                            tma_piece(sa + pc * PIECE_BYTES, am + pc, a_mn, T.m0, k0, Sg.a_z, aw, bar);
+                            tma_piece(sb + pc * PIECE_BYTES, bm + pc, b_mn, T.n0, k0, Sg.b_z, bw, bar);
+                        }
+                        ++q;
+                        ++done;
+                    }
+                }
+            }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t q = 0, tc = 0;
+            for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
+                const uint32_t buf = tc & 1u, use = tc >> 1;
+                if (use > 0 && !mbar_wait(smem_u32(&tempty_bar[buf]), (use - 1) & 1u)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + buf * TMEM_COLS;
+                for (;;) {
+                    const uint32_t slot = q % S;
+                    if (!mbar_wait(smem_u32(&full_bar[slot]), (q / S) & 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const StageMeta M = meta[slot];
+                    if (!(M.flags & 4)) {
+                        const uint32_t sa = sbase + slot * C::STAGE_BYTES;
+                        const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
+                        const uint32_t id = idesc(M.a_mn, M.b_mn, M.neg);
+                        for (int kk = 0; kk < M.k16; ++kk) {
+#pragma unroll
+                            for (int pr = 0; pr < (NSPLIT == 2 ? 3 : 1); ++pr) {
+                                const int pa = (pr == 2) ? 1 : 0;  // products: hi*hi, hi*lo, lo*hi
+                                const int pb = (pr == 1) ? 1 : 0;
+                                const uint32_t a_s = sa + pa * PIECE_BYTES;
+                                const uint32_t b_s = sb + pb * PIECE_BYTES;
+                                const uint64_t ad =
+                                    M.a_mn ? sdesc(a_s + kk * 2048, 8192, 1024) : sdesc(a_s + kk * 32, 16, 1024);
+                                const uint64_t bd =
+                                    M.b_mn ? sdesc(b_s + kk * 2048, 8192, 1024) : sdesc(b_s + kk * 32, 16, 1024);
+                                const uint32_t acc = ((M.flags & 1) && kk == 0 && pr == 0) ? 0u : 1u;
+                                mma_bf16(dt, ad, bd, id, acc);
+                            }
+                        }
+                    }
+                    mma_commit(smem_u32(&empty_bar[slot]));
+                    ++q;
+                    if (M.flags & 2) break;
+                }
+                if (failed) break;
+                mma_commit(smem_u32(&tfull_bar[buf]));
+            }
+            mma_commit(smem_u32(&drain_bar));
+            if (!mbar_wait(smem_u32(&drain_bar), 0)) failed = true;
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        uint32_t tc = 0;
+        for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
+            const uint32_t buf = tc & 1u, use = tc >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[buf]), use & 1u) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform (tcgen05.ld is warp-collective)
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            __syncwarp();
+            tc_fence_after();
+            const int tix = t % ntiles, v = t / ntiles;
+            const Tile T = tiles[tix];
+            const int nst = tile_stages_t(T, segs);
+            epilogue_tile<NSPLIT>(T, v, nst, tmem + buf * TMEM_COLS, warp, lane, B, smem_u32(&tempty_bar[buf]));
+        }
+    }
+    if (failed) atomicExch(B.err, 1);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -493,6 +721,189 @@ void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit
             attr = true;
         }
         tc_seg_gemm_kernel<1><<<grid, THREADS2, Cfg2<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
+    }
+    ++launch_counter();
+    DMRG_CHECK_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// TMA work lists and tensor maps (host)
+// ---------------------------------------------------------------------------
+
+void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<TSeg>& s, uint8_t mode,
+                            int64_t kchunk, float alpha) {
+    if (m <= 0 || n <= 0) return;
+    std::vector<std::pair<int, int>> chunks;
+    const bool atomic = (mode == TC_ATOMIC_F64 || mode == TC_ATOMIC_F32);
+    if (atomic && kchunk > 0) {
+        int beg = 0;
+        int64_t acc = 0;
+        for (int i = 0; i < (int)s.size(); ++i) {
+            if (acc > 0 && acc + s[i].k > kchunk) {
+                chunks.push_back({beg, i});
+                beg = i;
+                acc = 0;
+            }
+            acc += s[i].k;
+        }
+        chunks.push_back({beg, (int)s.size()});
+    } else {
+        chunks.push_back({0, (int)s.size()});
+    }
+    for (auto& ch : chunks) {
+        const int sb = (int)segs.size();
+        for (int i = ch.first; i < ch.second; ++i) segs.push_back(s[i]);
+        const int se = (int)segs.size();
+        for (int m0 = 0; m0 < m; m0 += TM)
+            for (int n0 = 0; n0 < n; n0 += TN) {
+                Tile t{};
+                t.alpha = alpha;
+                t.c_off = c_off;
+                t.ldc = ldc;
+                t.m = m;
+                t.n = n;
+                t.m0 = m0;
+                t.n0 = n0;
+                t.seg_beg = sb;
+                t.seg_end = se;
+                t.c_buf = (uint8_t)c_buf;
+                t.mode = mode;
+                tiles.push_back(t);
+            }
+    }
+}
+
+void TmaWorkList::upload(cudaStream_t st) {
+    if (tiles.size() > cap_tiles) {
+        if (d_tiles) cudaFree(d_tiles);
+        cap_tiles = tiles.size() + 16;
+        DMRG_CHECK_CUDA(cudaMalloc(&d_tiles, cap_tiles * sizeof(Tile)));
+    }
+    if (segs.size() > cap_segs) {
+        if (d_segs) cudaFree(d_segs);
+        cap_segs = segs.size() + 16;
+        DMRG_CHECK_CUDA(cudaMalloc(&d_segs, cap_segs * sizeof(TSeg)));
+    }
+    if (!tiles.empty())
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+    if (!segs.empty())
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(TSeg), cudaMemcpyHostToDevice, st));
+}
+
+void TmaWorkList::release() {
+    if (d_tiles) cudaFree(d_tiles);
+    if (d_segs) cudaFree(d_segs);
+    d_tiles = nullptr;
+    d_segs = nullptr;
+    cap_tiles = cap_segs = 0;
+}
+
+int MapTable::get(const MapKey& k) {
+    auto it = index.find(k);
+    if (it != index.end()) return it->second;
+    DMRG_REQUIRE(k.cols >= 1 && k.rows >= 1 && k.nz >= 1 && k.nv >= 1, DMRG_EINVAL, "empty tensor-map extent");
+    DMRG_REQUIRE(k.off % 8 == 0 && k.ld % 8 == 0 && k.zstride % 8 == 0 && k.vstride % 8 == 0, DMRG_EINVAL,
+                 "tensor-map operand not 16-byte aligned");
+    DMRG_REQUIRE(k.ld >= k.cols && k.zstride >= k.rows * k.ld && k.vstride >= k.nz * k.zstride, DMRG_EINVAL,
+                 "tensor-map strides overlap");
+    const int i = (int)keys.size();
+    keys.push_back(k);
+    index[k] = i;
+    return i;
+}
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        DMRG_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        DMRG_REQUIRE(q == cudaDriverEntryPointSuccess && p, DMRG_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+}  // namespace
+
+void MapTable::encode_upload(const TcBufs& tb, int nsplit, cudaStream_t st) {
+    const size_t n = 2 * keys.size();
+    std::vector<CUtensorMap> h(std::max<size_t>(n, 1));
+    EncodeTiledFn fn = encode_fn();
+    for (size_t i = 0; i < keys.size(); ++i) {
+        const MapKey& k = keys[i];
+        for (int pc = 0; pc < 2; ++pc) {
+            const __nv_bfloat16* base = pc == 0 ? tb.hi[k.buf] : tb.lo[k.buf];
+            if (pc == 1 && (nsplit < 2 || !base)) {
+                h[2 * i + 1] = h[2 * i];
+                continue;
+            }
+            DMRG_REQUIRE(base != nullptr, DMRG_EINVAL, "tensor map over an unset buffer");
+            const cuuint64_t dims[4] = {(cuuint64_t)k.cols, (cuuint64_t)k.rows, (cuuint64_t)k.nz, (cuuint64_t)k.nv};
+            const cuuint64_t strides[3] = {(cuuint64_t)k.ld * 2, (cuuint64_t)k.zstride * 2, (cuuint64_t)k.vstride * 2};
+            const cuuint32_t box[4] = {64, 64, 1, 1};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            const CUresult r = fn(&h[2 * i + pc], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(base + k.off), dims,
+                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            DMRG_REQUIRE(r == CUDA_SUCCESS, DMRG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        }
+    }
+    if (n > cap) {
+        if (d_maps) cudaFree(d_maps);
+        cap = n + 64;
+        DMRG_CHECK_CUDA(cudaMalloc(&d_maps, cap * sizeof(CUtensorMap)));
+    }
+    if (n > 0) DMRG_CHECK_CUDA(cudaMemcpyAsync(d_maps, h.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < kMaxBufs; ++b) {
+        enc_ptr[b][0] = tb.hi[b];
+        enc_ptr[b][1] = tb.lo[b];
+    }
+}
+
+bool MapTable::stale(const TcBufs& tb) const {
+    if (!d_maps) return true;
+    for (const MapKey& k : keys)
+        if (enc_ptr[k.buf][0] != tb.hi[k.buf] || enc_ptr[k.buf][1] != tb.lo[k.buf]) return true;
+    return false;
+}
+
+void MapTable::release() {
+    if (d_maps) cudaFree(d_maps);
+    d_maps = nullptr;
+    cap = 0;
+    clear();
+}
+
+void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBufs& b, int nvec, int nsplit,
+                         cudaStream_t st) {
+    if (w.tiles.empty()) return;
+    const int64_t total = (int64_t)w.tiles.size() * nvec;
+    DMRG_REQUIRE(total < (1LL << 31), DMRG_EINVAL, "tensor-core work list too large");
+    DMRG_REQUIRE(maps.d_maps != nullptr, DMRG_EINVAL, "tensor maps not uploaded");
+    const int grid = (int)std::min<int64_t>(total, tc_num_sms());
+    if (nsplit == 2) {
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CHECK_CUDA(
+                cudaFuncSetAttribute(tc_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<2>::SMEM));
+            attr = true;
+        }
+        tc_tma_kernel<2><<<grid, THREADS3, Cfg3<2>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
+                                                               maps.d_maps, b);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CHECK_CUDA(
+                cudaFuncSetAttribute(tc_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<1>::SMEM));
+            attr = true;
+        }
+        tc_tma_kernel<1><<<grid, THREADS3, Cfg3<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
+                                                               maps.d_maps, b);
     }
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());

@@ -2,6 +2,7 @@
 // products onto the segmented GEMM, environments (renormalisation, Eq.
 // Renorm), the bond's intermediates and sigma (Eq. Sigma), diag(H_eff).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <fstream>
@@ -233,6 +234,7 @@ void ProductList::clear() {
     outs.clear();
     cs.clear();
     chunks.clear();
+    tchunks.clear();
     flops = 0.0;
     scratch_elems = 0;
 }
@@ -242,6 +244,11 @@ void ProductList::release() {
         c.first.release();
         c.second.release();
     }
+    for (auto& c : tchunks) {
+        c.first.release();
+        c.second.release();
+    }
+    maps.release();
 }
 
 static Seg make_seg(const View& A, const View& B, int k, double alpha) {
@@ -431,6 +438,210 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
         }
         scratch_elems = std::max(scratch_elems, used);
         chunks.emplace_back(std::move(p1), std::move(p2));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged lowering
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Tensor-map key of view V read as a rows x cols matrix (before any transpose).
+MapKey view_key(const View& V, int64_t rows, int64_t cols, const int64_t* vstride, int nv) {
+    DMRG_REQUIRE(V.buf >= 0 && V.buf < kMaxBufs && !V.ident, DMRG_EINVAL, "tensor map of an implicit operand");
+    MapKey k{};
+    k.buf = V.buf;
+    k.off = V.off - (int64_t)V.z * V.zstride;
+    k.cols = cols;
+    k.rows = rows;
+    k.ld = V.ld;
+    k.nz = V.nz;
+    k.zstride = V.nz > 1 ? V.zstride : round_up(rows * V.ld, 8);
+    const bool pv = vstride && vstride[V.buf] > 0;
+    k.nv = pv ? nv : 1;
+    k.vstride = pv ? vstride[V.buf] : k.nz * k.zstride;
+    return k;
+}
+
+// out (m x n) += sign * op(A) (m x k) * op(B) (k x n) through tensor maps
+TSeg make_tseg(MapTable& mt, const View& A, const View& B, int m, int n, int k, double sign, const int64_t* vstride,
+               int nv) {
+    TSeg s{};
+    s.a_map = mt.get(view_key(A, A.tr ? k : m, A.tr ? m : k, vstride, nv));
+    s.b_map = mt.get(view_key(B, B.tr ? n : k, B.tr ? k : n, vstride, nv));
+    s.a_z = A.z;
+    s.b_z = B.z;
+    s.k = k;
+    s.a_tr = A.tr;
+    s.b_tr = B.tr;
+    s.a_pv = (vstride && vstride[A.buf] > 0) ? 1 : 0;
+    s.b_pv = (vstride && vstride[B.buf] > 0) ? 1 : 0;
+    s.sign = sign < 0.0 ? -1.0f : 1.0f;
+    return s;
+}
+
+}  // namespace
+
+void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t kchunk, uint8_t out_mode,
+                            const int64_t* vstride_in, int nv) {
+    const int8_t sbuf = sbuf_;
+    this->sbuf = sbuf_;
+    release();
+    tchunks.clear();
+    maps.clear();
+    flops = 0.0;
+    scratch_elems = 0;
+    tc = true;
+    View I;
+    I.buf = ibuf;
+    I.off = 0;
+    I.ld = ild;
+    // per-vector strides; the scratch holds one copy per vector, its stride (the
+    // largest chunk's need) is set once the chunks are known
+    int64_t vstride[kMaxBufs];
+    for (int b = 0; b < kMaxBufs; ++b) vstride[b] = vstride_in ? vstride_in[b] : 0;
+    vstride[sbuf] = round_up(std::max<int64_t>(cap, 8), 8);
+    struct Item {
+        int kind = 0;  // 3: three factors; 2: scaled two-factor product; 1: direct segment
+        bool pq_first = true;
+        int tr = 0, tcl = 0;  // phase-1 product rows / columns
+        int grp = -1, z = 0;
+        View X, Y;            // direct / scaled two-factor operands
+        int k = 0;
+        double fl = 0.0;  // algorithmic FLOPs of a kind 1 / 2 item
+    };
+    size_t i = 0;
+    while (i < cs.size()) {
+        // pass 1: the items of this chunk, their phase-1 shapes and scratch groups
+        std::vector<Item> items;
+        std::map<std::pair<int, int>, int> gidx;
+        std::vector<std::array<int64_t, 4>> groups;  // rows, cols, count, base
+        int64_t used = 0;
+        size_t j = i;
+        for (; j < cs.size(); ++j) {
+            const Contrib& c = cs[j];
+            const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
+            const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
+            Item it;
+            if (nreal == 3) {
+                const double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                const double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                it.kind = 3;
+                it.pq_first = cost_pq <= cost_qr;
+                it.tr = it.pq_first ? c.m : c.k1;
+                it.tcl = it.pq_first ? c.k2 : c.n;
+            } else {
+                if (nreal == 2) {
+                    if (c.P.ident) {
+                        it.X = c.Q;
+                        it.Y = c.R;
+                        it.k = c.k2;
+                    } else if (c.R.ident) {
+                        it.X = c.P;
+                        it.Y = c.Q;
+                        it.k = c.k1;
+                    } else {
+                        it.X = c.P;
+                        it.Y = c.R;
+                        it.k = c.k1;
+                    }
+                    it.fl = 2.0 * c.m * c.n * it.k;
+                } else {
+                    it.X = !c.P.ident ? c.P : (!c.Q.ident ? c.Q : c.R);
+                    it.Y = I;
+                    it.k = c.n;
+                    it.fl = 2.0 * c.m * c.n;
+                }
+                it.kind = unit ? 1 : 2;
+                if (!unit) {
+                    it.tr = c.m;
+                    it.tcl = c.n;
+                }
+            }
+            int64_t need = 0;
+            if (it.kind >= 2) need = (int64_t)it.tr * round_up(it.tcl, 8);
+            if (used + need > cap && used > 0) break;
+            if (it.kind >= 2) {
+                auto key = std::make_pair(it.tr, it.tcl);
+                auto g = gidx.find(key);
+                if (g == gidx.end()) {
+                    g = gidx.emplace(key, (int)groups.size()).first;
+                    groups.push_back({(int64_t)it.tr, (int64_t)it.tcl, 0, 0});
+                }
+                it.grp = g->second;
+                it.z = (int)groups[it.grp][2]++;
+            }
+            used += need;
+            items.push_back(it);
+        }
+        int64_t base = 0;
+        for (auto& g : groups) {
+            g[3] = base;
+            base += g[2] * g[0] * round_up(g[1], 8);
+        }
+        // pass 2: work lists
+        TmaWorkList p1, p2;
+        std::map<int, std::vector<TSeg>> segs;
+        std::vector<int> order;
+        for (size_t q = 0; q < items.size(); ++q) {
+            const Contrib& c = cs[i + q];
+            const Item& it = items[q];
+            if (!segs.count(c.out)) order.push_back(c.out);
+            std::vector<TSeg>& sv = segs[c.out];
+            View T;
+            if (it.kind >= 2) {
+                const auto& g = groups[it.grp];
+                T.buf = sbuf;
+                T.ld = (int)round_up(g[1], 8);
+                T.zstride = g[0] * T.ld;
+                T.nz = (int)g[2];
+                T.z = it.z;
+                T.off = g[3] + (int64_t)it.z * T.zstride;
+            }
+            if (it.kind == 3) {
+                if (it.pq_first) {
+                    flops += 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                    p1.add_block(T.off, sbuf, c.m, c.k2, T.ld, {make_tseg(maps, c.P, c.Q, c.m, c.k2, c.k1, 1.0, vstride, nv)},
+                                 TC_STORE_SPLIT, 0, (float)c.alpha);
+                    sv.push_back(make_tseg(maps, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv));
+                } else {
+                    flops += 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                    p1.add_block(T.off, sbuf, c.k1, c.n, T.ld, {make_tseg(maps, c.Q, c.R, c.k1, c.n, c.k2, 1.0, vstride, nv)},
+                                 TC_STORE_SPLIT, 0, (float)c.alpha);
+                    sv.push_back(make_tseg(maps, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv));
+                }
+            } else if (it.kind == 2) {
+                flops += it.fl;
+                p1.add_block(T.off, sbuf, c.m, c.n, T.ld, {make_tseg(maps, it.X, it.Y, c.m, c.n, it.k, 1.0, vstride, nv)},
+                             TC_STORE_SPLIT, 0, (float)c.alpha);
+                sv.push_back(make_tseg(maps, T, I, c.m, c.n, c.n, 1.0, vstride, nv));
+            } else {
+                flops += it.fl;
+                sv.push_back(make_tseg(maps, it.X, it.Y, c.m, c.n, it.k, c.alpha, vstride, nv));
+            }
+        }
+        for (int o : order) {
+            const OutBlock& ob = outs[o];
+            p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 1.0f);
+        }
+        scratch_elems = std::max(scratch_elems, used);
+        tchunks.emplace_back(std::move(p1), std::move(p2));
+        i = j;
+    }
+    // the scratch's per-vector stride is now known
+    scratch_elems = round_up(std::max<int64_t>(scratch_elems, 8), 8);
+    for (MapKey& k : maps.keys)
+        if (k.buf == sbuf) k.vstride = scratch_elems;
+    maps.index.clear();
+}
+
+void ProductList::run_tma(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st) {
+    for (auto& c : tchunks) {
+        DMRG_REQUIRE(c.first.tiles.empty() || (sbuf >= 0 && tb.out[sbuf]), DMRG_EINVAL,
+                     "tensor-core product list run without its scratch buffer");
+        launch_seg_gemm_tma(c.first, maps, tb, nvec, nsplit, st);
+        launch_seg_gemm_tma(c.second, maps, tb, nvec, nsplit, st);
     }
 }
 

@@ -26,12 +26,16 @@ struct MPSHost {
 
 // Operand view of a dense matrix stored in buffer `buf`: element (i, j) at
 // off + i*ld + j, or off + j*ld + i when tr.  `ident` marks the identity.
+// Operators of one stored family with the same block structure are nz
+// matrices zstride apart: this one is number z (off includes z * zstride).
 struct View {
     int8_t buf = -1;
     int64_t off = 0;
     int ld = 0;
     bool tr = false;
     bool ident = false;
+    int32_t z = 0, nz = 1;
+    int64_t zstride = 0;
     View T() const {
         View v = *this;
         v.tr = !v.tr;
@@ -73,6 +77,15 @@ struct ProductList {
     void upload(cudaStream_t st);
     void run(const BufTable& bt, int nvec, cudaStream_t st);
     void run_tc(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st);
+    // TMA-staged tensor-core engine: as lower_tc, with every operand read through
+    // a tensor map (maps); phase-1 products of equal shape share a 3-D scratch
+    // tensor.  vec_bufs: buffers holding one copy per vector (stride vstride[b],
+    // nv copies); the maps are encoded later by maps.encode_upload.
+    void lower_tma(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk,
+                   uint8_t out_mode, const int64_t* vstride, int nv);
+    void run_tma(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st);
+    std::vector<std::pair<TmaWorkList, TmaWorkList>> tchunks;
+    MapTable maps;
     void release();
 };
 

@@ -1,7 +1,11 @@
 // Tensor-core (tcgen05, sm_103a) segmented grouped GEMM on bf16 operand pieces.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
+
+#include <map>
+#include <tuple>
 
 #include "engine.h"
 
@@ -33,6 +37,68 @@ struct TcBufs {
 void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit, cudaStream_t st);
 
 int tc_num_sms();
+
+// ---------------------------------------------------------------------------
+// TMA-staged variant: every operand is addressed through a tensor map.
+// ---------------------------------------------------------------------------
+
+// A segment whose operands are read through tensor maps.  Each map is 4-D over
+// one bf16 piece: x = column, y = row, z = operator row of a stored family
+// (0 otherwise), w = vector index (for per-vector buffers).  The maps of a key
+// come in piece order (hi, then lo) at 2 * key and 2 * key + 1.
+struct TSeg {
+    int32_t a_map, b_map;  // map keys
+    int32_t a_z, b_z;      // z coordinates
+    int32_t k;             // K extent of the segment
+    uint8_t a_tr, b_tr;    // a_tr: A held as K x M (MN-major); b_tr: B held as N x K (K-major)
+    uint8_t a_pv, b_pv;    // 1: the operand's w coordinate is the vector index
+    float sign;            // +1 or -1 (MMA negate bit)
+};
+
+struct TmaWorkList {
+    std::vector<Tile> tiles;
+    std::vector<TSeg> segs;
+    Tile* d_tiles = nullptr;
+    TSeg* d_segs = nullptr;
+    size_t cap_tiles = 0, cap_segs = 0;
+    // output block (m x n, ld ldc) at c_off of c_buf, 128 x 128 tiles, split into
+    // K-chunks of at most kchunk (atomic modes only)
+    void add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<TSeg>& s, uint8_t mode,
+                   int64_t kchunk, float alpha);
+    void upload(cudaStream_t st);
+    void release();
+};
+
+// A matrix as a tensor-map key: element (z, y, x) of vector w of buffer `buf`
+// lives at off + w*vstride + z*zstride + y*ld + x (elements), x < cols, y < rows.
+struct MapKey {
+    int buf;
+    int64_t off;
+    int64_t cols, rows, ld, nz, zstride, nv, vstride;
+    auto tie() const { return std::tie(buf, off, cols, rows, ld, nz, zstride, nv, vstride); }
+    bool operator<(const MapKey& o) const { return tie() < o.tie(); }
+};
+
+struct MapTable {
+    std::vector<MapKey> keys;
+    std::map<MapKey, int> index;
+    CUtensorMap* d_maps = nullptr;
+    size_t cap = 0;
+    const void* enc_ptr[kMaxBufs][2] = {};  // piece pointers the device maps were encoded with
+    int get(const MapKey& k);  // validates alignment; returns the key index
+    bool stale(const TcBufs& tb) const;  // a piece pointer moved since the last encode
+    // encode 2 maps per key (pieces of tb.hi / tb.lo) and copy them to the device
+    void encode_upload(const TcBufs& tb, int nsplit, cudaStream_t st);
+    void clear() {
+        keys.clear();
+        index.clear();
+    }
+    void release();
+};
+
+// Launch the TMA-staged kernel over the tiles of `w` (maps on the device).
+void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBufs& b, int nvec, int nsplit,
+                         cudaStream_t st);
 
 // FP64 (unpadded rows of length n, ld_src) -> bf16 pieces (rows padded to ld_dst)
 void dev_split_f64(const double* src, int64_t rows, int n, int64_t ld_src, __nv_bfloat16* hi,
