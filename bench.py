@@ -36,7 +36,7 @@ WORKLOADS = {
     "k24_d500": dict(K=24, N=24, twoS=0, D=500, n_chol=96, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
 }
 METRIC = "sigma=H*psi TFLOP/s, s/site at K=73,D=3000; mixed vs FP64 at dE<=1e-6 Eh"
-PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2, "bf16x6": 3}
 # bounded sample the CPU oracle runs for the baseline (same recipe, small K)
 CPU_SAMPLE = dict(K=14, N=14, twoS=0, D=600, n_chol=56, ell=3.0, h_min=-4.0, wn=1.0, ws=1.0)
 
@@ -321,6 +321,43 @@ def run_mine(args):
         torch.distributed.destroy_process_group()
 
 
+def run_sigma_probe(args):
+    """--sigma-only: plan at the middle bond, then --warmup + --steps sigma calls,
+    each inside an NVTX range "sigma" (what the committed ncu summaries capture).
+    Prints one JSON line with the sigma timings; not the benchmark contract line."""
+    import torch
+    import paper_2311_02854_gb300 as g
+
+    w = WORKLOADS[args.workload]
+    K, D = w["K"], w["D"]
+    k = K // 2
+    td = tempfile.mkdtemp(prefix="dmrg_sigma_")
+    h, L, bonds, path = make_inputs(w, td, k)
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision])
+    plan.set_bond(k)
+    x = torch.from_numpy(si.random_vector(plan.dim, seed=1)).cuda()
+    y = torch.empty_like(x)
+    st = plan.stats()
+    ms = []
+    for i in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("sigma")
+        e0.record()
+        plan.sigma(x, y)
+        e1.record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    print(json.dumps({"mode": "sigma-only", "workload": args.workload, "precision": args.precision,
+                      "sigma_ms": round(t, 3), "sigma_tflops": round(st["sigma_flops"] / t / 1e9, 3),
+                      "sigma_flops": st["sigma_flops"], "tiles": st["sigma_tiles"], "stages": st["sigma_stages"],
+                      "mma_flops": st["sigma_mma_flops"], "store_bytes": st["store_bytes"]}), flush=True)
+    plan.close()
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -364,9 +401,13 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sigma-only", action="store_true",
+                    help="time sigma calls at the middle bond (NVTX range 'sigma'); for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sigma_only:
+        run_sigma_probe(args)
     else:
         run_mine(args)
 

@@ -65,8 +65,10 @@ typedef enum {
  *   tensor cores with FP32 accumulation in tensor memory; sigma is summed
  *   into FP64.  Davidson, orthogonalisation, Ritz, residuals, energies and
  *   decimation stay FP64.
- * BF16: as BF16X3 with only the hi part (one product per tile). */
-typedef enum { DMRG_FP64 = 0, DMRG_BF16X3 = 1, DMRG_BF16 = 2 } dmrg_precision;
+ * BF16: as BF16X3 with only the hi part (one product per tile).
+ * BF16X6: three pieces x = hi + lo + lo2 (24 significant bits, FP32-like
+ *   storage) and the six products whose piece orders sum to at most 2. */
+typedef enum { DMRG_FP64 = 0, DMRG_BF16X3 = 1, DMRG_BF16 = 2, DMRG_BF16X6 = 3 } dmrg_precision;
 
 typedef enum { DMRG_PRECOND_JACOBI = 0, DMRG_PRECOND_MLP = 1 } dmrg_precond;
 
@@ -109,6 +111,7 @@ typedef struct {
     int64_t sigma_tiles[2];       /* mixed sigma: 128 x 128 output tiles of phase 1 / phase 2 */
     int64_t sigma_stages[2];      /* mixed sigma: 64-deep K stages of phase 1 / phase 2 */
     double sigma_mma_flops;       /* mixed sigma: tensor work of the tiles (one bf16 product) */
+    int64_t sigma_maps;           /* mixed sigma: tensor maps of the current bond */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

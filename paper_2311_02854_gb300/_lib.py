@@ -9,7 +9,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
-DMRG_FP64, DMRG_BF16X3, DMRG_BF16 = 0, 1, 2
+DMRG_FP64, DMRG_BF16X3, DMRG_BF16, DMRG_BF16X6 = 0, 1, 2, 3
 DMRG_PRECOND_JACOBI, DMRG_PRECOND_MLP = 0, 1
 STATUS = {0: "DMRG_OK", -1: "DMRG_EINVAL", -2: "DMRG_ENOMEM", -3: "DMRG_ECUDA", -4: "DMRG_ENUMERIC",
           -5: "DMRG_ETIMEOUT", -6: "DMRG_ENOTCONV", -7: "DMRG_EIO"}
@@ -37,7 +37,7 @@ class Stats(C.Structure):
                 ("interm_bytes", C.c_int64), ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("precond_fallbacks", C.c_int64), ("davidson_iters_last", C.c_int),
                 ("ms_host_plan", C.c_double), ("sigma_tiles", C.c_int64 * 2), ("sigma_stages", C.c_int64 * 2),
-                ("sigma_mma_flops", C.c_double)]
+                ("sigma_mma_flops", C.c_double), ("sigma_maps", C.c_int64)]
 
     def as_dict(self):
         d = {}

@@ -18,11 +18,13 @@ enum : int8_t { BUF_L = 0, BUF_R = 1, BUF_INT = 2, BUF_PSI = 3, BUF_SCR = 4, BUF
 
 constexpr int64_t kChunkF64 = 1 << 14;  // K-depth per accumulation pass (FP64 engine)
 // Tensor cores: K-depth one output tile accumulates in FP32 tensor memory
-// before it is added (atomically) into the wider result.  The error of a chain
+// before it is added (atomically) into an FP64 result.  The error of a chain
 // grows linearly with its depth (about 6e-6 relative at 1024 on sigma-like
-// sums), so chains are kept short.
-constexpr int64_t kChunkTC = 1024;       // renormalisation and intermediates (FP32 result)
-constexpr int64_t kChunkSigmaTC = 1024;  // sigma (FP64 result)
+// sums), so chains are kept short; the operator store (renormalisation,
+// intermediates), whose error every later bond inherits, uses the shortest.
+constexpr int64_t kChunkTC = 256;        // renormalisation and intermediates
+constexpr int64_t kChunkSigmaTC = 1024;  // sigma, two pieces
+constexpr int64_t kChunkSigmaX6 = 256;   // sigma, three pieces
 
 struct OpLookup {
     bool ok = false;
@@ -93,13 +95,6 @@ double host_ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-float* alloc_f32(Plan& P, int64_t n) { return (float*)P.alloc_bf16(2 * n); }
-void free_f32(Plan& P, float*& p, int64_t n) {
-    __nv_bfloat16* q = (__nv_bfloat16*)p;
-    P.free_bf16(q, 2 * n);
-    p = nullptr;
-}
-
 void ensure_counter(Plan& P) {
     if (!P.d_ctr) {
         DMRG_CHECK_CUDA(cudaMalloc(&P.d_ctr, 2 * sizeof(int)));
@@ -115,14 +110,26 @@ TcBufs tc_base(Plan& P) {
     return tb;
 }
 
+// piece pointers of buffer b (n elements per piece)
+void set_pieces(const Plan& P, TcBufs& tb, int b, const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t n) {
+    tb.hi[b] = hi;
+    tb.lo[b] = lo;
+    tb.pstride[b] = P.nsplit == 3 ? n : 0;
+}
+void set_out_pieces(const Plan& P, TcBufs& tb, int b, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t n) {
+    tb.out[b] = hi;
+    tb.out_lo[b] = lo;
+    tb.out_pstride[b] = P.nsplit == 3 ? n : 0;
+}
+
 // bf16 pieces of the padded wavefunction copy for n elements (all vectors of a launch)
 void ensure_psi_pieces(Plan& P, int64_t n) {
     if (n <= P.n_ppc) return;
     P.free_bf16(P.ps_hi, P.n_ppc);
-    P.free_bf16(P.ps_lo, P.n_ppc);
+    P.free_lo(P.ps_lo, P.n_ppc);
     P.n_ppc = n;
     P.ps_hi = P.alloc_bf16(n);
-    P.ps_lo = P.alloc_bf16(n);
+    P.ps_lo = P.alloc_lo(n);
 }
 
 // Buffers of the mixed sigma at bond k (out: FP64 result of vector 0)
@@ -133,24 +140,17 @@ TcBufs sigma_bufs(Plan& P, int k, double* out) {
     const Block& R = *P.right[k + 1];
     const int64_t per = std::max<int64_t>(P.sigma_tc.scratch_elems, 8);
     TcBufs tb = tc_base(P);
-    tb.hi[BUF_L] = L.h;
-    tb.lo[BUF_L] = L.l;
-    tb.hi[BUF_R] = R.h;
-    tb.lo[BUF_R] = R.l;
-    tb.hi[BUF_INT] = P.interm.h;
-    tb.lo[BUF_INT] = P.interm.l;
-    tb.hi[BUF_PSI] = P.ps_hi;
-    tb.lo[BUF_PSI] = P.ps_lo;
+    set_pieces(P, tb, BUF_L, L.h, L.l, L.n);
+    set_pieces(P, tb, BUF_R, R.h, R.l, R.n);
+    set_pieces(P, tb, BUF_INT, P.interm.h, P.interm.l, P.interm.n);
+    set_pieces(P, tb, BUF_PSI, P.ps_hi, P.ps_lo, P.n_ppc);
     tb.vstride[BUF_PSI] = P.dim_pad;
-    tb.hi[BUF_SCR] = P.s_hi;
-    tb.lo[BUF_SCR] = P.s_lo;
+    set_pieces(P, tb, BUF_SCR, P.s_hi, P.s_lo, P.n_spc);
     tb.vstride[BUF_SCR] = per;
-    tb.hi[BUF_ID] = P.id_hi;
-    tb.lo[BUF_ID] = P.id_lo;
+    set_pieces(P, tb, BUF_ID, P.id_hi, P.id_lo, (int64_t)P.id_n * P.id_n);
     tb.out[BUF_OUT] = out;
     tb.out_vstride[BUF_OUT] = P.dim;
-    tb.out[BUF_SCR] = P.s_hi;
-    tb.out_lo[BUF_SCR] = P.s_lo;
+    set_out_pieces(P, tb, BUF_SCR, P.s_hi, P.s_lo, P.n_spc);
     tb.out_vstride[BUF_SCR] = per;
     return tb;
 }
@@ -161,7 +161,7 @@ void free_block(Plan& P, std::unique_ptr<Block>& b) {
     if (!b) return;
     P.free(b->d, b->n);
     P.free_bf16(b->h, b->n);
-    P.free_bf16(b->l, b->n);
+    P.free_lo(b->l, b->n);
     b.reset();
 }
 
@@ -179,12 +179,12 @@ void ensure_ident(Plan& P, int n) {
     }
     if (P.mixed() && P.id_n != P.ident_n) {
         P.free_bf16(P.id_hi, (int64_t)P.id_n * P.id_n);
-        P.free_bf16(P.id_lo, (int64_t)P.id_n * P.id_n);
+        P.free_lo(P.id_lo, (int64_t)P.id_n * P.id_n);
         P.id_n = P.ident_n;
         const int64_t nn = (int64_t)P.id_n * P.id_n;
         P.id_hi = P.alloc_bf16(nn);
-        P.id_lo = P.alloc_bf16(nn);
-        dev_split_f64(P.d_ident, 1, (int)nn, nn, P.id_hi, P.id_lo, nn, P.stream);
+        P.id_lo = P.alloc_lo(nn);
+        dev_split_f64(P.d_ident, 1, (int)nn, nn, P.id_hi, P.id_lo, nn, P.stream, P.lo2(P.id_lo, nn));
     }
 }
 
@@ -192,10 +192,10 @@ void ensure_scratch(Plan& P, int64_t n) {
     if (P.mixed()) {
         if (n <= P.n_spc) return;
         P.free_bf16(P.s_hi, P.n_spc);
-        P.free_bf16(P.s_lo, P.n_spc);
+        P.free_lo(P.s_lo, P.n_spc);
         P.n_spc = n;
         P.s_hi = P.alloc_bf16(n);
-        P.s_lo = P.alloc_bf16(n);
+        P.s_lo = P.alloc_lo(n);
         return;
     }
     if (n <= P.n_scratch) return;
@@ -235,7 +235,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     flops = 0.0;
     if (P.mixed()) {
         S.h = P.alloc_bf16(S.n);
-        S.l = P.alloc_bf16(S.n);
+        S.l = P.alloc_lo(S.n);
     } else {
         S.d = P.alloc(S.n);
     }
@@ -259,7 +259,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
         s.a_buf = BUF_W;
         s.b_buf = (uint8_t)IF.owner;  // BUF_L or BUF_R
         s.alpha = 1.0;
-        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_ATOMIC_F32, kChunkTC, 128, 1.0f);
+        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_ATOMIC_F64, kChunkTC, 128, 1.0f);
         else wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TILE_STORE);
         woff += (int64_t)nr * ldw;
     }
@@ -275,29 +275,27 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     if (P.mixed()) {
         if (wn > P.n_wpc) {
             P.free_bf16(P.w_hi, P.n_wpc);
-            P.free_bf16(P.w_lo, P.n_wpc);
+            P.free_lo(P.w_lo, P.n_wpc);
             P.n_wpc = wn;
             P.w_hi = P.alloc_bf16(wn);
-            P.w_lo = P.alloc_bf16(wn);
+            P.w_lo = P.alloc_lo(wn);
         }
-        dev_split_f64(P.d_wcoef, 1, (int)wn, wn, P.w_hi, P.w_lo, wn, P.stream);
+        dev_split_f64(P.d_wcoef, 1, (int)wn, wn, P.w_hi, P.w_lo, wn, P.stream, P.lo2(P.w_lo, P.n_wpc));
         // FP32 sum of the K-chunks, then split into the bf16 pieces
-        float* acc = alloc_f32(P, S.n);
-        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, S.n * 4, P.stream));
+        double* acc = P.alloc(S.n);  // FP64 sum of the K-chunks, then split into the pieces
+        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, S.n * 8, P.stream));
         TcBufs tb = tc_base(P);
         for (int o = 0; o < 2; ++o)
             if (blocks[o]) {
-                tb.hi[o] = blocks[o]->h;
-                tb.lo[o] = blocks[o]->l;
+                set_pieces(P, tb, o, blocks[o]->h, blocks[o]->l, blocks[o]->n);
             }
-        tb.hi[BUF_W] = P.w_hi;
-        tb.lo[BUF_W] = P.w_lo;
+        set_pieces(P, tb, BUF_W, P.w_hi, P.w_lo, P.n_wpc);
         tb.out[BUF_INT] = acc;
         launch_seg_gemm_tc(wl, tb, 1, P.nsplit, P.stream);
         P.check_device_error();
-        dev_split_f32(acc, S.n, S.h, S.l, P.stream);
+        dev_split_f64_flat(acc, S.n, S.h, S.l, P.stream, P.lo2(S.l, S.n));
         DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
-        free_f32(P, acc, S.n);
+        P.free(acc, S.n);
     } else {
         BufTable bt{};
         bt.p[BUF_L] = blocks[0] ? blocks[0]->d : nullptr;
@@ -313,7 +311,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
 void free_interms(Plan& P, IntermStore& S) {
     P.free(S.d, S.n);
     P.free_bf16(S.h, S.n);
-    P.free_bf16(S.l, S.n);
+    P.free_lo(S.l, S.n);
     S.n = 0;
 }
 
@@ -330,9 +328,9 @@ std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end) {
     B->n = std::max<int64_t>(B->lay.total, 32);
     if (P.mixed()) {
         B->h = P.alloc_bf16(B->n);
-        B->l = P.alloc_bf16(B->n);
+        B->l = P.alloc_lo(B->n);
         DMRG_CHECK_CUDA(cudaMemsetAsync(B->h, 0, B->n * 2, P.stream));
-        DMRG_CHECK_CUDA(cudaMemsetAsync(B->l, 0, B->n * 2, P.stream));
+        DMRG_CHECK_CUDA(cudaMemsetAsync(B->l, 0, P.lo_pieces() * B->n * 2, P.stream));
     } else {
         B->d = P.alloc(B->n);
         dev_fill(B->d, 0.0, B->n, P.stream);
@@ -381,8 +379,8 @@ static SiteDev upload_site(Plan& P, int k) {
     DMRG_CHECK_CUDA(cudaMemcpyAsync(S.d, host.data(), S.n * 8, cudaMemcpyHostToDevice, P.stream));
     if (P.mixed()) {
         S.h = P.alloc_bf16(S.n);
-        S.l = P.alloc_bf16(S.n);
-        dev_split_f64(S.d, 1, (int)S.n, S.n, S.h, S.l, S.n, P.stream);
+        S.l = P.alloc_lo(S.n);
+        dev_split_f64(S.d, 1, (int)S.n, S.n, S.h, S.l, S.n, P.stream, P.lo2(S.l, S.n));
     }
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     return S;
@@ -391,7 +389,7 @@ static SiteDev upload_site(Plan& P, int k) {
 static void free_site(Plan& P, SiteDev& S) {
     P.free(S.d, S.n);
     P.free_bf16(S.h, S.n);
-    P.free_bf16(S.l, S.n);
+    P.free_lo(S.l, S.n);
 }
 
 // Grow block X by site m (forward: X = sites 1..m-1 -> sites 1..m) or
@@ -531,33 +529,27 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     ensure_ident(P, maxd);
     const int64_t cap = scratch_cap(P);
     if (P.mixed()) {
-        pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F32);
+        pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F64);
         P.stats.ms_host_plan += host_ms_since(host0);
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 8));
         pl.upload(P.stream);
-        float* acc = alloc_f32(P, out->n);
-        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, out->n * 4, P.stream));
+        double* acc = P.alloc(out->n);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(acc, 0, out->n * 8, P.stream));
         TcBufs tb = tc_base(P);
-        tb.hi[BUF_L] = X.h;
-        tb.lo[BUF_L] = X.l;
-        tb.hi[BUF_INT] = IS.h;
-        tb.lo[BUF_INT] = IS.l;
-        tb.hi[BUF_PSI] = A.h;
-        tb.lo[BUF_PSI] = A.l;
-        tb.hi[BUF_SCR] = P.s_hi;
-        tb.lo[BUF_SCR] = P.s_lo;
-        tb.hi[BUF_ID] = P.id_hi;
-        tb.lo[BUF_ID] = P.id_lo;
+        set_pieces(P, tb, BUF_L, X.h, X.l, X.n);
+        set_pieces(P, tb, BUF_INT, IS.h, IS.l, IS.n);
+        set_pieces(P, tb, BUF_PSI, A.h, A.l, A.n);
+        set_pieces(P, tb, BUF_SCR, P.s_hi, P.s_lo, P.n_spc);
+        set_pieces(P, tb, BUF_ID, P.id_hi, P.id_lo, (int64_t)P.id_n * P.id_n);
         tb.out[BUF_R] = acc;
-        tb.out[BUF_SCR] = P.s_hi;
-        tb.out_lo[BUF_SCR] = P.s_lo;
+        set_out_pieces(P, tb, BUF_SCR, P.s_hi, P.s_lo, P.n_spc);
         pl.run_tc(tb, 1, P.nsplit, P.stream);
         P.check_device_error();
         out->h = P.alloc_bf16(out->n);
-        out->l = P.alloc_bf16(out->n);
-        dev_split_f32(acc, out->n, out->h, out->l, P.stream);
+        out->l = P.alloc_lo(out->n);
+        dev_split_f64_flat(acc, out->n, out->h, out->l, P.stream, P.lo2(out->l, out->n));
         DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
-        free_f32(P, acc, out->n);
+        P.free(acc, out->n);
     } else {
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, kChunkF64);
         P.stats.ms_host_plan += host_ms_since(host0);
@@ -726,7 +718,8 @@ void set_bond(Plan& P, int k) {
         int64_t vs[kMaxBufs] = {};
         vs[BUF_PSI] = P.dim_pad;
         tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, std::max<int64_t>(scratch_cap(P) / G, 1 << 20),
-                     P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : kChunkSigmaTC, TC_ATOMIC_F64, vs, G);
+                     P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC),
+                     TC_ATOMIC_F64, vs, G);
         tl.cs.clear();
         for (int ph = 0; ph < 2; ++ph) P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
         P.stats.sigma_mma_flops = 0.0;
@@ -748,6 +741,7 @@ void set_bond(Plan& P, int k) {
             ch.second.upload(P.stream);
         }
         tl.maps.encode_upload(sigma_bufs(P, k, nullptr), P.nsplit, P.stream);
+        P.stats.sigma_maps = (int64_t)tl.maps.keys.size();
         P.stats.sigma_flops = tl.flops;
         // padded bf16 copy of psi: one split job per sector
         std::vector<SplitJob> jobs;
@@ -841,6 +835,11 @@ BufTable bond_buffers(Plan& P, const double* psi, double* out) {
         bt.lo[BUF_R] = R.l;
         bt.p[BUF_INT] = (double*)P.interm.h;
         bt.lo[BUF_INT] = P.interm.l;
+        if (P.nsplit == 3) {
+            bt.pstride[BUF_L] = L.n;
+            bt.pstride[BUF_R] = R.n;
+            bt.pstride[BUF_INT] = P.interm.n;
+        }
         bt.pmask = (1u << BUF_L) | (1u << BUF_R) | (1u << BUF_INT);
     } else {
         bt.p[BUF_L] = L.d;
@@ -900,7 +899,8 @@ void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
         const int nv = std::min(G, nvec - v0);
         for (int v = 0; v < nv; ++v)
             dev_split_blocks(psi + (int64_t)(v0 + v) * P.dim, P.d_psi_jobs, P.n_psi_jobs,
-                             P.ps_hi + (int64_t)v * P.dim_pad, P.ps_lo + (int64_t)v * P.dim_pad, st);
+                             P.ps_hi + (int64_t)v * P.dim_pad, P.ps_lo + (int64_t)v * P.dim_pad, st,
+                             P.nsplit == 3 ? P.ps_lo + P.n_ppc + (int64_t)v * P.dim_pad : nullptr);
         DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v0 * P.dim, 0, (size_t)nv * P.dim * 8, st));
         const TcBufs tb = sigma_bufs(P, P.bond, out + (int64_t)v0 * P.dim);
         if (tl.maps.stale(tb)) tl.maps.encode_upload(tb, P.nsplit, st);

@@ -88,15 +88,16 @@ dmrg_status grouped_gemm_tc(int nsplit, int n_out, const int* m, const int* n, c
     eb = round_up(eb, 8);
     __nv_bfloat16 *ha = nullptr, *la = nullptr, *hb = nullptr, *lb = nullptr;
     int* ctr = nullptr;
+    const int lop = nsplit == 3 ? 2 : 1;  // pieces held in the lo arrays
     DMRG_CHECK_CUDA(cudaMalloc(&ha, ea * 2));
-    DMRG_CHECK_CUDA(cudaMalloc(&la, ea * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&la, lop * ea * 2));
     DMRG_CHECK_CUDA(cudaMalloc(&hb, eb * 2));
-    DMRG_CHECK_CUDA(cudaMalloc(&lb, eb * 2));
+    DMRG_CHECK_CUDA(cudaMalloc(&lb, lop * eb * 2));
     DMRG_CHECK_CUDA(cudaMalloc(&ctr, 2 * sizeof(int)));
     DMRG_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st));
     DMRG_REQUIRE(ea < 2147483647 && eb < 2147483647, DMRG_EINVAL, "operand too large");
-    dev_split_f64(a, 1, (int)ea_n, ea_n, ha, la, ea, st);
-    dev_split_f64(b, 1, (int)eb_n, eb_n, hb, lb, eb, st);
+    dev_split_f64(a, 1, (int)ea_n, ea_n, ha, la, ea, st, nsplit == 3 ? la + ea : nullptr);
+    dev_split_f64(b, 1, (int)eb_n, eb_n, hb, lb, eb, st, nsplit == 3 ? lb + eb : nullptr);
     if (ec > 0) DMRG_CHECK_CUDA(cudaMemsetAsync(c, 0, ec * 8, st));
     wl.upload(st);
     TcBufs tb{};
@@ -104,6 +105,10 @@ dmrg_status grouped_gemm_tc(int nsplit, int n_out, const int* m, const int* n, c
     tb.lo[0] = la;
     tb.hi[1] = hb;
     tb.lo[1] = lb;
+    if (nsplit == 3) {
+        tb.pstride[0] = ea;
+        tb.pstride[1] = eb;
+    }
     tb.out[2] = c;
     tb.counter = ctr;
     tb.err = ctr + 1;
@@ -173,6 +178,7 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         if (P.opt.precision == DMRG_FP64) P.nsplit = 0;
         else if (P.opt.precision == DMRG_BF16X3) P.nsplit = 2;
         else if (P.opt.precision == DMRG_BF16) P.nsplit = 1;
+        else if (P.opt.precision == DMRG_BF16X6) P.nsplit = 3;
         else throw Error(DMRG_EINVAL, "unknown precision mode");
         P.K = K;
         P.N = N;
@@ -401,11 +407,11 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
                               const int64_t* b_off, const int* ldb, const int* b_tr, const double* alpha,
                               const double* a, const double* b, double* c, void* stream) {
     if (n_out < 0 || !m || !n || !c_off || !seg_beg || !a || !b || !c) return fail(nullptr, DMRG_EINVAL, "bad arguments");
-    if (precision != DMRG_FP64 && precision != DMRG_BF16X3 && precision != DMRG_BF16)
+    if (precision != DMRG_FP64 && precision != DMRG_BF16X3 && precision != DMRG_BF16 && precision != DMRG_BF16X6)
         return fail(nullptr, DMRG_EINVAL, "unknown precision");
     if (precision != DMRG_FP64) {
         try {
-            return grouped_gemm_tc(precision == DMRG_BF16X3 ? 2 : 1, n_out, m, n, c_off, seg_beg, k, a_off, lda, a_tr,
+            return grouped_gemm_tc(precision == DMRG_BF16X3 ? 2 : (precision == DMRG_BF16X6 ? 3 : 1), n_out, m, n, c_off, seg_beg, k, a_off, lda, a_tr,
                                    b_off, ldb, b_tr, alpha, a, b, c, (cudaStream_t)stream);
         } catch (const Error& e) {
             return fail(nullptr, e.code, e.what());

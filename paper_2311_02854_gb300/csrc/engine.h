@@ -29,7 +29,8 @@ struct Tile {
     int32_t ldc, m, n;    // block leading dim and extents
     int32_t m0, n0;       // tile origin inside the block
     int32_t seg_beg, seg_end;
-    uint8_t c_buf, mode, pad0, pad1;
+    uint8_t c_buf, mode;
+    uint16_t nst;         // tensor-core engine: 64-deep K stages of the tile (set by the TMA work list)
     float alpha;          // epilogue scale (tensor-core engine; the FP64 engine scales per segment)
 };
 
@@ -42,6 +43,7 @@ struct BufTable {
     // buffers whose bit is set in pmask hold bf16 pieces: p[i] is the hi piece
     // (as raw bf16) and lo[i] the lo piece (may be null); they are read as hi + lo.
     const void* lo[kMaxBufs];
+    int64_t pstride[kMaxBufs];  // three pieces: piece 2 at lo + pstride (0: none)
     uint32_t pmask;
 };
 

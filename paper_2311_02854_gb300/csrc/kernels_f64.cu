@@ -105,7 +105,11 @@ __device__ __forceinline__ double ld_elem(const BufTable& bt, int buf, int64_t i
     if (bt.pmask & (1u << buf)) {
         const __nv_bfloat16* h = (const __nv_bfloat16*)bt.p[buf];
         double x = (double)__bfloat162float(h[idx]);
-        if (bt.lo[buf]) x += (double)__bfloat162float(((const __nv_bfloat16*)bt.lo[buf])[idx]);
+        if (bt.lo[buf]) {
+            const __nv_bfloat16* l = (const __nv_bfloat16*)bt.lo[buf];
+            x += (double)__bfloat162float(l[idx]);
+            if (bt.pstride[buf]) x += (double)__bfloat162float(l[bt.pstride[buf] + idx]);
+        }
         return x;
     }
     return bt.p[buf][idx];

@@ -16,6 +16,8 @@ namespace dmrg {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;
+static_assert(sizeof(Tile) % 4 == 0 && sizeof(TSeg) % 4 == 0, "work-list records are moved by 32-bit shuffles");
+static_assert(sizeof(TSeg) % 16 == 0, "segment records stay 16-byte aligned");
 constexpr int PIECE_BYTES = TM * TK * 2;  // one 128 x 64 bf16 operand tile
 constexpr uint32_t TMEM_COLS = 128;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded waits: 2 s
@@ -163,14 +165,23 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
 constexpr int kEpiWarps = 4, kProdWarps = 4;
 constexpr int NPROD = kProdWarps * 32;
 constexpr int THREADS2 = (kEpiWarps + kProdWarps + 1) * 32;
-constexpr int LAG = 2;  // producer arrives on a stage's full barrier LAG stages after issuing it
-
 template <int NSPLIT>
 struct Cfg2 {
-    static constexpr int STAGES = (NSPLIT == 1) ? 6 : 3;
+    static constexpr int STAGES = (NSPLIT == 1) ? 6 : (NSPLIT == 2 ? 3 : 2);
     static constexpr int STAGE_BYTES = 2 * NSPLIT * PIECE_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    // the producers publish a stage's full barrier LAG stages after issuing it
+    static constexpr int LAG = STAGES - 1 < 2 ? STAGES - 1 : 2;
 };
+
+// Piece products of a split-precision MMA: x = sum_i x_i with |x_i| ~ 2^-8i |x|;
+// products x_i y_j with i + j <= NSPLIT - 1 are kept (1, 3 or 6 of them).
+template <int NSPLIT>
+struct Prods {
+    static constexpr int N = NSPLIT == 1 ? 1 : (NSPLIT == 2 ? 3 : 6);
+};
+__device__ __forceinline__ int prod_a(int pr) { return (0x210100 >> (4 * pr)) & 0xF; }  // 0,0,1,0,1,2
+__device__ __forceinline__ int prod_b(int pr) { return (0x012010 >> (4 * pr)) & 0xF; }  // 0,1,0,2,1,0
 
 struct StageMeta {
     uint8_t a_mn, b_mn, neg, flags;  // flags: 1 first stage of a tile, 2 last, 4 no MMA (empty tile)
@@ -233,16 +244,19 @@ __device__ __forceinline__ void epilogue_tile(const Tile& T, int v, int nst, uin
 #pragma unroll
         for (int j0 = 0; j0 < TN; j0 += 8) {
             if (j0 >= ncol) break;
-            __align__(16) __nv_bfloat16 h8[8], l8[8];
+            __align__(16) __nv_bfloat16 h8[8], l8[8], m8[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const float x = alpha * __uint_as_float(acc[j0 + j]);
                 const __nv_bfloat16 h = __float2bfloat16_rn(x);
                 h8[j] = h;
-                l8[j] = __float2bfloat16_rn(x - __bfloat162float(h));
+                const float r = x - __bfloat162float(h);
+                l8[j] = __float2bfloat16_rn(r);
+                m8[j] = __float2bfloat16_rn(r - __bfloat162float(l8[j]));
             }
             *(uint4*)(oh + j0) = *(const uint4*)h8;
-            if (NSPLIT == 2) *(uint4*)(ol + j0) = *(const uint4*)l8;
+            if (NSPLIT >= 2) *(uint4*)(ol + j0) = *(const uint4*)l8;
+            if (NSPLIT == 3) *(uint4*)(ol + B.out_pstride[T.c_buf] + j0) = *(const uint4*)m8;
         }
     }
 }
@@ -299,6 +313,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
             if (qs >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[qs % S]), ((qs / S) - 1) & 1u)) return false;
             return true;
         };
+        constexpr int LAG = C::LAG;
         auto end_issue = [&]() {  // after committing stage q: publish stage q - LAG
             cp_async_commit();
             if (q >= (uint32_t)LAG) {
@@ -329,9 +344,15 @@ __global__ void __launch_bounds__(THREADS2, 1)
                     const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
                     load_piece(sa, B.hi[Sg.a_buf] + ao, Sg.lda, a_mn, T.m0, T.m, k0, Sg.k, p);
                     load_piece(sb, B.hi[Sg.b_buf] + bo, Sg.ldb, b_mn, T.n0, T.n, k0, Sg.k, p);
-                    if (NSPLIT == 2) {
+                    if (NSPLIT >= 2) {
                         load_piece(sa + PIECE_BYTES, B.lo[Sg.a_buf] + ao, Sg.lda, a_mn, T.m0, T.m, k0, Sg.k, p);
                         load_piece(sb + PIECE_BYTES, B.lo[Sg.b_buf] + bo, Sg.ldb, b_mn, T.n0, T.n, k0, Sg.k, p);
+                    }
+                    if (NSPLIT == 3) {
+                        load_piece(sa + 2 * PIECE_BYTES, B.lo[Sg.a_buf] + B.pstride[Sg.a_buf] + ao, Sg.lda, a_mn, T.m0,
+                                   T.m, k0, Sg.k, p);
+                        load_piece(sb + 2 * PIECE_BYTES, B.lo[Sg.b_buf] + B.pstride[Sg.b_buf] + bo, Sg.ldb, b_mn, T.n0,
+                                   T.n, k0, Sg.k, p);
                     }
                     if (p == 0) {
                         const int kv = min(TK, Sg.k - k0);
@@ -367,9 +388,8 @@ __global__ void __launch_bounds__(THREADS2, 1)
                         const uint32_t id = idesc(M.a_mn, M.b_mn, M.neg);
                         for (int kk = 0; kk < M.k16; ++kk) {
 #pragma unroll
-                            for (int pr = 0; pr < (NSPLIT == 2 ? 3 : 1); ++pr) {
-                                const int pa = (pr == 2) ? 1 : 0;  // products: hi*hi, hi*lo, lo*hi
-                                const int pb = (pr == 1) ? 1 : 0;
+                            for (int pr = 0; pr < Prods<NSPLIT>::N; ++pr) {
+                                const int pa = prod_a(pr), pb = prod_b(pr);
                                 const uint32_t a_s = sa + pa * PIECE_BYTES;
                                 const uint32_t b_s = sb + pb * PIECE_BYTES;
                                 const uint64_t ad =
@@ -439,24 +459,22 @@ __device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, 
         : "memory");
 }
 
-__device__ __forceinline__ int tile_stages_t(const Tile& T, const TSeg* __restrict__ segs) {
-    int nst = 0;
-    for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + TK - 1) / TK;
-    return nst;
-}
 
-// One 128 x 64 operand piece as two 64 x 64 boxes.  K-major (mn = 0): rows
-// r0.. of the map at x = k0; MN-major (mn = 1): columns r0.. of the map at
-// rows k0..  Shared layout: K-major rows at 128 B (8-row groups 1 KB apart);
-// MN-major 64-element M halves 8 KB apart, 8-row K groups 1 KB apart.
+// One 128 x 64 operand piece as (up to) two 64-row boxes.  K-major (mn = 0):
+// rows r0.. of the map at x = k0; MN-major (mn = 1): columns r0.. of the map
+// at rows k0..  Shared layout: K-major rows at 128 B (8-row groups 1 KB
+// apart); MN-major 64-element halves 8 KB apart, 8-row K groups 1 KB apart.
+// With halves = 1 the second half is not loaded (the block ends within the
+// first 64 rows / columns; the MMA reads don't-care data there, which only
+// reaches output rows / columns the epilogue drops).
 __device__ __forceinline__ void tma_piece(uint32_t dst, const CUtensorMap* map, int mn, int r0, int k0, int z, int w,
-                                          uint32_t bar) {
+                                          uint32_t bar, int halves) {
     if (!mn) {
         tma_load4(dst, map, k0, r0, z, w, bar);
-        tma_load4(dst + 8192, map, k0, r0 + 64, z, w, bar);
+        if (halves == 2) tma_load4(dst + 8192, map, k0, r0 + 64, z, w, bar);
     } else {
         tma_load4(dst, map, r0, k0, z, w, bar);
-        tma_load4(dst + 8192, map, r0 + 64, k0, z, w, bar);
+        if (halves == 2) tma_load4(dst + 8192, map, r0 + 64, k0, z, w, bar);
     }
 }
 
@@ -466,10 +484,21 @@ constexpr int THREADS3 = (kEpiWarps + 2) * 32;
 
 template <int NSPLIT>
 struct Cfg3 {
-    static constexpr int STAGES = (NSPLIT == 1) ? 6 : 3;
+    static constexpr int STAGES = (NSPLIT == 1) ? 6 : (NSPLIT == 2 ? 3 : 2);
     static constexpr int STAGE_BYTES = 2 * NSPLIT * PIECE_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
 };
+
+// stage record of the TMA kernel
+struct StageMeta3 {
+    uint8_t a_mn, b_mn, neg, flags;  // flags: 1 first stage of a tile, 2 last, 4 no MMA (empty tile)
+    uint8_t k16, n16, pad[2];        // 16-deep K steps holding data; MMA N / 16
+};
+
+__device__ __forceinline__ uint32_t idesc_n(int a_mn, int b_mn, int neg, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg << 13) | ((uint32_t)a_mn << 15) |
+           ((uint32_t)b_mn << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
 template <int NSPLIT>
 __global__ void __launch_bounds__(THREADS3, 1)
@@ -479,7 +508,7 @@ __global__ void __launch_bounds__(THREADS3, 1)
     constexpr int S = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2], drain_bar;
-    __shared__ StageMeta meta[S];
+    __shared__ StageMeta3 meta[S];
     __shared__ uint32_t tmem_base_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -517,13 +546,16 @@ __global__ void __launch_bounds__(THREADS3, 1)
             for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
                 const int tix = t % ntiles, v = t / ntiles;
                 const Tile T = tiles[tix];
-                const int nst = tile_stages_t(T, segs);
+                const int nst = T.nst;
+                // a second 64-row (or 64-column) half only when the block extends past the first
+                const int nA = (T.m - T.m0 > 64) ? 2 : 1, nB = (T.n - T.n0 > 64) ? 2 : 1;
+                const int n16 = (min(TN, T.n - T.n0) + 15) / 16;
                 if (nst == 0) {
                     if (q >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[q % S]), ((q / S) - 1) & 1u)) {
                         failed = true;
                         break;
                     }
-                    meta[q % S] = StageMeta{0, 0, 0, 1 | 2 | 4, 0};
+                    meta[q % S] = StageMeta3{0, 0, 0, 1 | 2 | 4, 0, 0, {0, 0}};
                     mbar_arrive(smem_u32(&full_bar[q % S]));
                     ++q;
                     continue;
@@ -533,8 +565,9 @@ __global__ void __launch_bounds__(THREADS3, 1)
                     const TSeg Sg = segs[s];
                     const int a_mn = Sg.a_tr ? 1 : 0, b_mn = Sg.b_tr ? 0 : 1;
                     const int aw = Sg.a_pv ? v : 0, bw = Sg.b_pv ? v : 0;
-                    const CUtensorMap* am = maps + 2 * Sg.a_map;
-                    const CUtensorMap* bm = maps + 2 * Sg.b_map;
+                    const CUtensorMap* am = maps + 3 * Sg.a_map;
+                    const CUtensorMap* bm = maps + 3 * Sg.b_map;
+                    const uint32_t bytes = (uint32_t)NSPLIT * 128u * (uint32_t)(nA * Sg.a_br + nB * Sg.b_br);
                     for (int k0 = 0; k0 < Sg.k; k0 += TK) {
                         const uint32_t slot = q % S;
                         if (q >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[slot]), ((q / S) - 1) & 1u)) {
@@ -542,17 +575,17 @@ __global__ void __launch_bounds__(THREADS3, 1)
                             break;
                         }
                         const int kv = min(TK, Sg.k - k0);
-                        meta[slot] = StageMeta{(uint8_t)a_mn, (uint8_t)b_mn, (uint8_t)(Sg.sign < 0.f ? 1 : 0),
-                                               (uint8_t)((done == 0 ? 1 : 0) | (done == nst - 1 ? 2 : 0)),
-                                               (kv + 15) / 16};
+                        meta[slot] = StageMeta3{(uint8_t)a_mn, (uint8_t)b_mn, (uint8_t)(Sg.sign < 0.f ? 1 : 0),
+                                                (uint8_t)((done == 0 ? 1 : 0) | (done == nst - 1 ? 2 : 0)),
+                                                (uint8_t)((kv + 15) / 16), (uint8_t)n16, {0, 0}};
                         const uint32_t bar = smem_u32(&full_bar[slot]);
-                        mbar_arrive_tx(bar, (uint32_t)C::STAGE_BYTES);
+                        mbar_arrive_tx(bar, bytes);
                         const uint32_t sa = sbase + slot * C::STAGE_BYTES;
                         const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
 #pragma unroll
                         for (int pc = 0; pc < NSPLIT; ++pc) {
-                            tma_piece(sa + pc * PIECE_BYTES, am + pc, a_mn, T.m0, k0, Sg.a_z, aw, bar);
-                            tma_piece(sb + pc * PIECE_BYTES, bm + pc, b_mn, T.n0, k0, Sg.b_z, bw, bar);
+                            tma_piece(sa + pc * PIECE_BYTES, am + pc, a_mn, T.m0, k0, Sg.a_z, aw, bar, nA);
+                            tma_piece(sb + pc * PIECE_BYTES, bm + pc, b_mn, T.n0, k0, Sg.b_z, bw, bar, nB);
                         }
                         ++q;
                         ++done;
@@ -579,16 +612,15 @@ __global__ void __launch_bounds__(THREADS3, 1)
                         break;
                     }
                     tc_fence_after();
-                    const StageMeta M = meta[slot];
+                    const StageMeta3 M = meta[slot];
                     if (!(M.flags & 4)) {
                         const uint32_t sa = sbase + slot * C::STAGE_BYTES;
                         const uint32_t sb = sa + NSPLIT * PIECE_BYTES;
-                        const uint32_t id = idesc(M.a_mn, M.b_mn, M.neg);
+                        const uint32_t id = idesc_n(M.a_mn, M.b_mn, M.neg, 16 * M.n16);
                         for (int kk = 0; kk < M.k16; ++kk) {
 #pragma unroll
-                            for (int pr = 0; pr < (NSPLIT == 2 ? 3 : 1); ++pr) {
-                                const int pa = (pr == 2) ? 1 : 0;  // products: hi*hi, hi*lo, lo*hi
-                                const int pb = (pr == 1) ? 1 : 0;
+                            for (int pr = 0; pr < Prods<NSPLIT>::N; ++pr) {
+                                const int pa = prod_a(pr), pb = prod_b(pr);
                                 const uint32_t a_s = sa + pa * PIECE_BYTES;
                                 const uint32_t b_s = sb + pb * PIECE_BYTES;
                                 const uint64_t ad =
@@ -613,8 +645,12 @@ __global__ void __launch_bounds__(THREADS3, 1)
     } else {
         // ---------------- epilogue ----------------
         uint32_t tc = 0;
+        Tile Tn{};
+        if (blockIdx.x < total) Tn = tiles[blockIdx.x % ntiles];
         for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
             const uint32_t buf = tc & 1u, use = tc >> 1;
+            const Tile T = Tn;  // fetched one tile ahead, while the MMAs of this one run
+            if (t + (int)gridDim.x < total) Tn = tiles[(t + gridDim.x) % ntiles];
             int ok = 1;
             if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[buf]), use & 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform (tcgen05.ld is warp-collective)
@@ -624,10 +660,8 @@ __global__ void __launch_bounds__(THREADS3, 1)
             }
             __syncwarp();
             tc_fence_after();
-            const int tix = t % ntiles, v = t / ntiles;
-            const Tile T = tiles[tix];
-            const int nst = tile_stages_t(T, segs);
-            epilogue_tile<NSPLIT>(T, v, nst, tmem + buf * TMEM_COLS, warp, lane, B, smem_u32(&tempty_bar[buf]));
+            epilogue_tile<NSPLIT>(T, t / ntiles, T.nst, tmem + buf * TMEM_COLS, warp, lane, B,
+                                  smem_u32(&tempty_bar[buf]));
         }
     }
     if (failed) atomicExch(B.err, 1);
@@ -644,39 +678,49 @@ __global__ void __launch_bounds__(THREADS3, 1)
 // conversions
 // ---------------------------------------------------------------------------
 
+// x -> hi (+ lo (+ lo2)): each piece is the bf16 rounding of what the previous ones leave
+__device__ __forceinline__ void split3(double xd, __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2,
+                                      int64_t i) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)xd);
+    hi[i] = h;
+    if (lo) {
+        const double r = xd - (double)__bfloat162float(h);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)r);
+        lo[i] = l;
+        if (lo2) lo2[i] = __float2bfloat16_rn((float)(r - (double)__bfloat162float(l)));
+    }
+}
+
 __global__ void split_f64_kernel(const double* __restrict__ src, int64_t rows, int n, int64_t lds,
-                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ldd) {
+                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ldd,
+                                 __nv_bfloat16* __restrict__ lo2) {
     const int64_t tot = rows * ldd;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / ldd, c = i % ldd;
-        const float x = (c < n) ? (float)src[r * lds + c] : 0.0f;
-        const double xd = (c < n) ? src[r * lds + c] : 0.0;
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi[i] = h;
-        if (lo) lo[i] = __float2bfloat16_rn((float)(xd - (double)__bfloat162float(h)));
+        split3((c < n) ? src[r * lds + c] : 0.0, hi, lo, lo2, i);
     }
+}
+
+__global__ void split_f64_flat_kernel(const double* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ hi,
+                                      __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        split3(src[i], hi, lo, lo2, i);
 }
 
 __global__ void split_f32_kernel(const float* __restrict__ src, int64_t n, __nv_bfloat16* __restrict__ hi,
-                                 __nv_bfloat16* __restrict__ lo) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float x = src[i];
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi[i] = h;
-        if (lo) lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
-    }
+                                 __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        split3((double)src[i], hi, lo, lo2, i);
 }
 
 __global__ void split_blocks_kernel(const double* __restrict__ src, const SplitJob* __restrict__ jobs,
-                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                    __nv_bfloat16* __restrict__ lo2) {
     const SplitJob J = jobs[blockIdx.x];
     const int64_t tot = (int64_t)J.rows * J.ld_dst;
     for (int64_t i = threadIdx.x; i < tot; i += blockDim.x) {
         const int r = (int)(i / J.ld_dst), c = (int)(i % J.ld_dst);
-        const double xd = (c < J.cols) ? src[J.src_off + (int64_t)r * J.ld_src + c] : 0.0;
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)xd);
-        hi[J.dst_off + i] = h;
-        if (lo) lo[J.dst_off + i] = __float2bfloat16_rn((float)(xd - (double)__bfloat162float(h)));
+        split3((c < J.cols) ? src[J.src_off + (int64_t)r * J.ld_src + c] : 0.0, hi, lo, lo2, J.dst_off + i);
     }
 }
 
@@ -705,7 +749,15 @@ void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit
     DMRG_REQUIRE(total < (1LL << 31), DMRG_EINVAL, "tensor-core work list too large");
     DMRG_CHECK_CUDA(cudaMemsetAsync(b.counter, 0, sizeof(int), st));
     const int grid = (int)std::min<int64_t>(total, tc_num_sms());
-    if (nsplit == 2) {
+    if (nsplit == 3) {
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_seg_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg2<3>::SMEM));
+            attr = true;
+        }
+        tc_seg_gemm_kernel<3><<<grid, THREADS2, Cfg2<3>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs, b);
+    } else if (nsplit == 2) {
         static bool attr = false;
         if (!attr) {
             DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_seg_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -752,7 +804,12 @@ void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, con
     }
     for (auto& ch : chunks) {
         const int sb = (int)segs.size();
-        for (int i = ch.first; i < ch.second; ++i) segs.push_back(s[i]);
+        int64_t nst = 0;
+        for (int i = ch.first; i < ch.second; ++i) {
+            segs.push_back(s[i]);
+            nst += (s[i].k + TK - 1) / TK;
+        }
+        DMRG_REQUIRE(nst < 65536, DMRG_EINVAL, "tile with too many K stages (use a K-chunk)");
         const int se = (int)segs.size();
         for (int m0 = 0; m0 < m; m0 += TM)
             for (int n0 = 0; n0 < n; n0 += TN) {
@@ -768,6 +825,7 @@ void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, con
                 t.seg_end = se;
                 t.c_buf = (uint8_t)c_buf;
                 t.mode = mode;
+                t.nst = (uint16_t)nst;
                 tiles.push_back(t);
             }
     }
@@ -830,23 +888,24 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 void MapTable::encode_upload(const TcBufs& tb, int nsplit, cudaStream_t st) {
-    const size_t n = 2 * keys.size();
+    const size_t n = 3 * keys.size();
     std::vector<CUtensorMap> h(std::max<size_t>(n, 1));
     EncodeTiledFn fn = encode_fn();
     for (size_t i = 0; i < keys.size(); ++i) {
         const MapKey& k = keys[i];
-        for (int pc = 0; pc < 2; ++pc) {
-            const __nv_bfloat16* base = pc == 0 ? tb.hi[k.buf] : tb.lo[k.buf];
-            if (pc == 1 && (nsplit < 2 || !base)) {
-                h[2 * i + 1] = h[2 * i];
+        for (int pc = 0; pc < 3; ++pc) {
+            const __nv_bfloat16* base =
+                pc == 0 ? tb.hi[k.buf] : (pc == 1 ? tb.lo[k.buf] : (tb.lo[k.buf] ? tb.lo[k.buf] + tb.pstride[k.buf] : nullptr));
+            if (pc >= nsplit || !base) {  // unused piece: a copy of the hi map
+                h[3 * i + pc] = h[3 * i];
                 continue;
             }
             DMRG_REQUIRE(base != nullptr, DMRG_EINVAL, "tensor map over an unset buffer");
             const cuuint64_t dims[4] = {(cuuint64_t)k.cols, (cuuint64_t)k.rows, (cuuint64_t)k.nz, (cuuint64_t)k.nv};
             const cuuint64_t strides[3] = {(cuuint64_t)k.ld * 2, (cuuint64_t)k.zstride * 2, (cuuint64_t)k.vstride * 2};
-            const cuuint32_t box[4] = {64, 64, 1, 1};
+            const cuuint32_t box[4] = {64, (cuuint32_t)box_rows(k.rows), 1, 1};
             const cuuint32_t estr[4] = {1, 1, 1, 1};
-            const CUresult r = fn(&h[2 * i + pc], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(base + k.off), dims,
+            const CUresult r = fn(&h[3 * i + pc], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)(base + k.off), dims,
                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             DMRG_REQUIRE(r == CUDA_SUCCESS, DMRG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -862,13 +921,16 @@ void MapTable::encode_upload(const TcBufs& tb, int nsplit, cudaStream_t st) {
     for (int b = 0; b < kMaxBufs; ++b) {
         enc_ptr[b][0] = tb.hi[b];
         enc_ptr[b][1] = tb.lo[b];
+        enc_ptr[b][2] = tb.lo[b] ? tb.lo[b] + tb.pstride[b] : nullptr;
     }
 }
 
 bool MapTable::stale(const TcBufs& tb) const {
     if (!d_maps) return true;
     for (const MapKey& k : keys)
-        if (enc_ptr[k.buf][0] != tb.hi[k.buf] || enc_ptr[k.buf][1] != tb.lo[k.buf]) return true;
+        if (enc_ptr[k.buf][0] != tb.hi[k.buf] || enc_ptr[k.buf][1] != tb.lo[k.buf] ||
+            enc_ptr[k.buf][2] != (tb.lo[k.buf] ? tb.lo[k.buf] + tb.pstride[k.buf] : nullptr))
+            return true;
     return false;
 }
 
@@ -886,11 +948,18 @@ void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBuf
     DMRG_REQUIRE(total < (1LL << 31), DMRG_EINVAL, "tensor-core work list too large");
     DMRG_REQUIRE(maps.d_maps != nullptr, DMRG_EINVAL, "tensor maps not uploaded");
     const int grid = (int)std::min<int64_t>(total, tc_num_sms());
-    if (nsplit == 2) {
+    if (nsplit == 3) {
         static bool attr = false;
         if (!attr) {
-            DMRG_CHECK_CUDA(
-                cudaFuncSetAttribute(tc_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<2>::SMEM));
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<3>::SMEM));
+            attr = true;
+        }
+        tc_tma_kernel<3><<<grid, THREADS3, Cfg3<3>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
+                                                        maps.d_maps, b);
+    } else if (nsplit == 2) {
+        static bool attr = false;
+        if (!attr) {
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<2>::SMEM));
             attr = true;
         }
         tc_tma_kernel<2><<<grid, THREADS3, Cfg3<2>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
@@ -898,8 +967,7 @@ void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBuf
     } else {
         static bool attr = false;
         if (!attr) {
-            DMRG_CHECK_CUDA(
-                cudaFuncSetAttribute(tc_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<1>::SMEM));
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<1>::SMEM));
             attr = true;
         }
         tc_tma_kernel<1><<<grid, THREADS3, Cfg3<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
@@ -910,24 +978,33 @@ void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBuf
 }
 
 void dev_split_f64(const double* src, int64_t rows, int n, int64_t ld_src, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                   int64_t ld_dst, cudaStream_t st) {
+                   int64_t ld_dst, cudaStream_t st, __nv_bfloat16* lo2) {
     if (rows <= 0) return;
-    split_f64_kernel<<<grid_for(rows * ld_dst), 256, 0, st>>>(src, rows, n, ld_src, hi, lo, ld_dst);
+    split_f64_kernel<<<grid_for(rows * ld_dst), 256, 0, st>>>(src, rows, n, ld_src, hi, lo, ld_dst, lo2);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
 }
 
-void dev_split_f32(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st) {
+void dev_split_f64_flat(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st,
+                        __nv_bfloat16* lo2) {
     if (n <= 0) return;
-    split_f32_kernel<<<grid_for(n), 256, 0, st>>>(src, n, hi, lo);
+    split_f64_flat_kernel<<<grid_for(n), 256, 0, st>>>(src, n, hi, lo, lo2);
+    ++launch_counter();
+    DMRG_CHECK_CUDA(cudaGetLastError());
+}
+
+void dev_split_f32(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st,
+                   __nv_bfloat16* lo2) {
+    if (n <= 0) return;
+    split_f32_kernel<<<grid_for(n), 256, 0, st>>>(src, n, hi, lo, lo2);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
 }
 
 void dev_split_blocks(const double* src, const SplitJob* d_jobs, int njobs, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                      cudaStream_t st) {
+                      cudaStream_t st, __nv_bfloat16* lo2) {
     if (njobs <= 0) return;
-    split_blocks_kernel<<<njobs, 256, 0, st>>>(src, d_jobs, hi, lo);
+    split_blocks_kernel<<<njobs, 256, 0, st>>>(src, d_jobs, hi, lo, lo2);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
 }

@@ -193,28 +193,28 @@ Plan::~Plan() {
         if (b) {
             if (b->d) free(b->d, b->n);
             free_bf16(b->h, b->n);
-            free_bf16(b->l, b->n);
+            free_lo(b->l, b->n);
         }
     for (auto& b : right)
         if (b) {
             if (b->d) free(b->d, b->n);
             free_bf16(b->h, b->n);
-            free_bf16(b->l, b->n);
+            free_lo(b->l, b->n);
         }
     free_bf16(s_hi, n_spc);
-    free_bf16(s_lo, n_spc);
+    free_lo(s_lo, n_spc);
     free_bf16(ps_hi, n_ppc);
-    free_bf16(ps_lo, n_ppc);
+    free_lo(ps_lo, n_ppc);
     free_bf16(id_hi, (int64_t)id_n * id_n);
-    free_bf16(id_lo, (int64_t)id_n * id_n);
+    free_lo(id_lo, (int64_t)id_n * id_n);
     free_bf16(w_hi, n_wpc);
-    free_bf16(w_lo, n_wpc);
+    free_lo(w_lo, n_wpc);
     if (d_psi_jobs) cudaFree(d_psi_jobs);
     if (d_ctr) cudaFree(d_ctr);
     sigma_tc.release();
     free(interm.d, interm.n);
     free_bf16(interm.h, interm.n);
-    free_bf16(interm.l, interm.n);
+    free_lo(interm.l, interm.n);
     free(d_scratch, n_scratch);
     free(d_ident, (int64_t)ident_n * ident_n);
     free(d_wcoef, n_wcoef);
@@ -468,8 +468,12 @@ MapKey view_key(const View& V, int64_t rows, int64_t cols, const int64_t* vstrid
 TSeg make_tseg(MapTable& mt, const View& A, const View& B, int m, int n, int k, double sign, const int64_t* vstride,
                int nv) {
     TSeg s{};
-    s.a_map = mt.get(view_key(A, A.tr ? k : m, A.tr ? m : k, vstride, nv));
-    s.b_map = mt.get(view_key(B, B.tr ? n : k, B.tr ? k : n, vstride, nv));
+    const MapKey ka = view_key(A, A.tr ? k : m, A.tr ? m : k, vstride, nv);
+    const MapKey kb = view_key(B, B.tr ? n : k, B.tr ? k : n, vstride, nv);
+    s.a_map = mt.get(ka);
+    s.b_map = mt.get(kb);
+    s.a_br = (uint8_t)box_rows(ka.rows);
+    s.b_br = (uint8_t)box_rows(kb.rows);
     s.a_z = A.z;
     s.b_z = B.z;
     s.k = k;

@@ -111,8 +111,10 @@ struct Plan {
     MPSHost mps;
     QN tot;
     int K = 0, N = 0, twoS = 0, D = 0, n_so = 0;
-    int nsplit = 0;  // 0: FP64 engine; 1: bf16; 2: bf16 x3 (hi + lo)
+    int nsplit = 0;  // 0: FP64 engine; 1: bf16; 2: bf16 x3 (hi + lo); 3: bf16 x6 (hi + lo + lo2)
     bool mixed() const { return nsplit > 0; }
+    // the `lo` array of a piece buffer holds piece 1, then (three pieces) piece 2
+    int lo_pieces() const { return nsplit == 3 ? 2 : 1; }
     cudaStream_t stream = nullptr;
     std::string last_error;
     dmrg_stats_t stats{};
@@ -171,6 +173,10 @@ struct Plan {
     void free(double*& p, int64_t n);
     __nv_bfloat16* alloc_bf16(int64_t n);
     void free_bf16(__nv_bfloat16*& p, int64_t n);
+    __nv_bfloat16* alloc_lo(int64_t n) { return alloc_bf16(lo_pieces() * n); }
+    void free_lo(__nv_bfloat16*& p, int64_t n) { free_bf16(p, lo_pieces() * n); }
+    // piece 2 of a lo array of n elements per piece (null unless three pieces)
+    __nv_bfloat16* lo2(__nv_bfloat16* lo, int64_t n) const { return (nsplit == 3 && lo) ? lo + n : nullptr; }
     void check_device_error();
     ~Plan();
 };

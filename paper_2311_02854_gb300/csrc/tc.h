@@ -24,9 +24,11 @@ enum TcMode : uint8_t {
 struct TcBufs {
     const __nv_bfloat16* hi[kMaxBufs];
     const __nv_bfloat16* lo[kMaxBufs];
+    int64_t pstride[kMaxBufs];  // three pieces: piece 2 at lo + pstride
     int64_t vstride[kMaxBufs];
     void* out[kMaxBufs];       // double* / float* / bf16 hi pieces (by mode)
     void* out_lo[kMaxBufs];    // bf16 lo pieces for TC_STORE_SPLIT
+    int64_t out_pstride[kMaxBufs];
     int64_t out_vstride[kMaxBufs];
     int* counter;              // dynamic tile counter (zeroed before each launch)
     int* err;                  // device error word (0 = ok)
@@ -45,13 +47,15 @@ int tc_num_sms();
 // A segment whose operands are read through tensor maps.  Each map is 4-D over
 // one bf16 piece: x = column, y = row, z = operator row of a stored family
 // (0 otherwise), w = vector index (for per-vector buffers).  The maps of a key
-// come in piece order (hi, then lo) at 2 * key and 2 * key + 1.
+// come in piece order (hi, lo, lo2) at 3 * key + piece.
 struct TSeg {
     int32_t a_map, b_map;  // map keys
     int32_t a_z, b_z;      // z coordinates
     int32_t k;             // K extent of the segment
     uint8_t a_tr, b_tr;    // a_tr: A held as K x M (MN-major); b_tr: B held as N x K (K-major)
     uint8_t a_pv, b_pv;    // 1: the operand's w coordinate is the vector index
+    uint8_t a_br, b_br;    // rows of the maps' boxes (min(64, rows rounded up to 16))
+    uint8_t pad[2];
     float sign;            // +1 or -1 (MMA negate bit)
 };
 
@@ -71,6 +75,8 @@ struct TmaWorkList {
 
 // A matrix as a tensor-map key: element (z, y, x) of vector w of buffer `buf`
 // lives at off + w*vstride + z*zstride + y*ld + x (elements), x < cols, y < rows.
+// Its boxes are 64 columns x box_rows(rows) rows.
+inline int box_rows(int64_t rows) { return rows >= 64 ? 64 : (int)((rows + 15) / 16 * 16); }
 struct MapKey {
     int buf;
     int64_t off;
@@ -84,10 +90,10 @@ struct MapTable {
     std::map<MapKey, int> index;
     CUtensorMap* d_maps = nullptr;
     size_t cap = 0;
-    const void* enc_ptr[kMaxBufs][2] = {};  // piece pointers the device maps were encoded with
+    const void* enc_ptr[kMaxBufs][3] = {};  // piece pointers the device maps were encoded with
     int get(const MapKey& k);  // validates alignment; returns the key index
     bool stale(const TcBufs& tb) const;  // a piece pointer moved since the last encode
-    // encode 2 maps per key (pieces of tb.hi / tb.lo) and copy them to the device
+    // encode 3 maps per key (pieces hi, lo, lo + pstride) and copy them to the device
     void encode_upload(const TcBufs& tb, int nsplit, cudaStream_t st);
     void clear() {
         keys.clear();
@@ -100,17 +106,22 @@ struct MapTable {
 void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBufs& b, int nvec, int nsplit,
                          cudaStream_t st);
 
-// FP64 (unpadded rows of length n, ld_src) -> bf16 pieces (rows padded to ld_dst)
+// FP64 (unpadded rows of length n, ld_src) -> bf16 pieces (rows padded to ld_dst);
+// lo2 (optional) receives the third piece x - hi - lo
 void dev_split_f64(const double* src, int64_t rows, int n, int64_t ld_src, __nv_bfloat16* hi,
-                   __nv_bfloat16* lo, int64_t ld_dst, cudaStream_t st);
+                   __nv_bfloat16* lo, int64_t ld_dst, cudaStream_t st, __nv_bfloat16* lo2 = nullptr);
+// FP64 -> bf16 pieces, same layout, n elements
+void dev_split_f64_flat(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st,
+                        __nv_bfloat16* lo2 = nullptr);
 // FP32 -> bf16 pieces, same layout, n elements
-void dev_split_f32(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st);
+void dev_split_f32(const float* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st,
+                   __nv_bfloat16* lo2 = nullptr);
 // batched block copy FP64 -> pieces: for each job (src_off, dst_off, rows, cols, ld_src, ld_dst)
 struct SplitJob {
     int64_t src_off, dst_off;
     int rows, cols, ld_src, ld_dst;
 };
 void dev_split_blocks(const double* src, const SplitJob* d_jobs, int njobs, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                      cudaStream_t st);
+                      cudaStream_t st, __nv_bfloat16* lo2 = nullptr);
 
 }  // namespace dmrg

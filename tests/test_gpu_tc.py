@@ -55,7 +55,7 @@ def _problem(rng, nblocks, sizes):
     return A, B, blocks, ref, bound, coff
 
 
-@pytest.mark.parametrize("precision,u", [(1, 2.0 ** -16), (2, 2.0 ** -8)])
+@pytest.mark.parametrize("precision,u", [(1, 2.0 ** -16), (2, 2.0 ** -8), (3, 2.0 ** -19)])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_tc_grouped_gemm_vs_fp64(precision, u, seed):
     torch = cuda_torch()
