@@ -90,6 +90,12 @@ typedef struct {
                                FP32 tensor memory before it is added into the FP64
                                result (0 => default 1024); shorter chains cost more
                                FP64 atomics and lose less to FP32 accumulation */
+    int fp64_store;         /* mixed modes: 1 = renormalise and form intermediates with the
+                               FP64 engine and keep that FP64 operator store, plus its bf16
+                               pieces for the tensor-core sigma (more memory and slower
+                               renormalisation; the store then carries no tensor-core
+                               accumulation error, and with fp64_final the energies are
+                               Rayleigh quotients of the FP64 Hamiltonian); default 0 */
 } dmrg_options;
 
 typedef struct {

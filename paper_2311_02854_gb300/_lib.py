@@ -25,7 +25,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_roots", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("max_space", C.c_int), ("precond", C.c_int), ("fp64_final", C.c_int),
                 ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
-                ("verbose", C.c_int), ("tc_kchunk", C.c_int64)]
+                ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -236,9 +236,8 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     if (P.mixed()) {
         S.h = P.alloc_bf16(S.n);
         S.l = P.alloc_lo(S.n);
-    } else {
-        S.d = P.alloc(S.n);
     }
+    if (P.f64_store()) S.d = P.alloc(S.n);
     if (im.fams.empty()) return;
     std::vector<double> W(std::max<int64_t>(wtot, 8), 0.0);
     WorkList wl;
@@ -246,7 +245,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     for (auto& IF : im.fams) {
         const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
         const int nr = (int)IF.rows.size(), no = f.nops();
-        const int ldw = P.mixed() ? (int)round_up(no, 8) : no;
+        const int ldw = P.tc_store() ? (int)round_up(no, 8) : no;
         for (int r = 0; r < nr; ++r)
             for (auto& rc : IF.rows[r]) W[woff + (int64_t)r * ldw + rc.first] += rc.second;
         DMRG_REQUIRE(f.stride < (1LL << 31), DMRG_EINVAL, "operator family too large");
@@ -259,7 +258,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
         s.a_buf = BUF_W;
         s.b_buf = (uint8_t)IF.owner;  // BUF_L or BUF_R
         s.alpha = 1.0;
-        if (P.mixed()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_ATOMIC_F64, kChunkTC, 128, 1.0f);
+        if (P.tc_store()) wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TC_ATOMIC_F64, kChunkTC, 128, 1.0f);
         else wl.add_block(IF.base, BUF_INT, nr, (int)f.nnz, (int)f.stride, {s}, TILE_STORE);
         woff += (int64_t)nr * ldw;
     }
@@ -272,7 +271,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     }
     DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_wcoef, W.data(), wn * 8, cudaMemcpyHostToDevice, P.stream));
     wl.upload(P.stream);
-    if (P.mixed()) {
+    if (P.tc_store()) {
         if (wn > P.n_wpc) {
             P.free_bf16(P.w_hi, P.n_wpc);
             P.free_lo(P.w_lo, P.n_wpc);
@@ -303,6 +302,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
         bt.p[BUF_INT] = S.d;
         bt.p[BUF_W] = P.d_wcoef;
         launch_seg_gemm_f64(wl, bt, 1, P.stream);
+        if (P.mixed()) dev_split_f64_flat(S.d, S.n, S.h, S.l, P.stream, P.lo2(S.l, S.n));
     }
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     wl.release();
@@ -331,7 +331,8 @@ std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end) {
         B->l = P.alloc_lo(B->n);
         DMRG_CHECK_CUDA(cudaMemsetAsync(B->h, 0, B->n * 2, P.stream));
         DMRG_CHECK_CUDA(cudaMemsetAsync(B->l, 0, P.lo_pieces() * B->n * 2, P.stream));
-    } else {
+    }
+    if (P.f64_store()) {
         B->d = P.alloc(B->n);
         dev_fill(B->d, 0.0, B->n, P.stream);
     }
@@ -528,7 +529,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     int maxd = std::max({XL.basis.dmax(), OL.basis.dmax(), 1});
     ensure_ident(P, maxd);
     const int64_t cap = scratch_cap(P);
-    if (P.mixed()) {
+    if (P.tc_store()) {
         pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F64);
         P.stats.ms_host_plan += host_ms_since(host0);
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 8));
@@ -553,7 +554,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     } else {
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, kChunkF64);
         P.stats.ms_host_plan += host_ms_since(host0);
-        ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
+        ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1));
         pl.upload(P.stream);
         out->d = P.alloc(out->n);
         DMRG_CHECK_CUDA(cudaMemsetAsync(out->d, 0, out->n * 8, P.stream));
@@ -565,6 +566,11 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
         bt.p[BUF_SCR] = P.d_scratch;
         bt.p[BUF_ID] = P.d_ident;
         pl.run(bt, 1, P.stream);
+        if (P.mixed()) {  // bf16 pieces of the FP64 store for the tensor-core sigma
+            out->h = P.alloc_bf16(out->n);
+            out->l = P.alloc_lo(out->n);
+            dev_split_f64_flat(out->d, out->n, out->h, out->l, P.stream, P.lo2(out->l, out->n));
+        }
     }
     cudaEventRecord(e1, P.stream);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
@@ -652,8 +658,9 @@ void set_bond(Plan& P, int k) {
     cudaEventDestroy(e1);
     P.stats.ms_interm += ms;
     P.stats.interm_flops = fl;
-    P.stats.interm_bytes = P.interm.n * (P.mixed() ? 4 : 8);
-    P.stats.store_bytes = (L.n + R.n) * (P.mixed() ? 4 : 8);
+    const int esz = (P.mixed() ? 2 * (1 + P.lo_pieces()) : 0) + (P.f64_store() ? 8 : 0);
+    P.stats.interm_bytes = P.interm.n * esz;
+    P.stats.store_bytes = (L.n + R.n) * esz;
 
     // sigma contributions (FP64 views; the bf16 copy of psi is padded)
     const auto hs0 = std::chrono::steady_clock::now();
@@ -828,7 +835,7 @@ BufTable bond_buffers(Plan& P, const double* psi, double* out) {
     BufTable bt{};
     const Block& L = *P.left[P.bond - 1];
     const Block& R = *P.right[P.bond + 1];
-    if (P.mixed()) {
+    if (P.tc_store()) {
         bt.p[BUF_L] = (double*)L.h;
         bt.lo[BUF_L] = L.l;
         bt.p[BUF_R] = (double*)R.h;

@@ -151,6 +151,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->keep_envs = 0;
     o->verbose = 0;
     o->tc_kchunk = 0;
+    o->fp64_store = 0;
 }
 
 const char* dmrg_version(void) {

@@ -113,6 +113,11 @@ struct Plan {
     int K = 0, N = 0, twoS = 0, D = 0, n_so = 0;
     int nsplit = 0;  // 0: FP64 engine; 1: bf16; 2: bf16 x3 (hi + lo); 3: bf16 x6 (hi + lo + lo2)
     bool mixed() const { return nsplit > 0; }
+    // the operator store exists only as bf16 pieces built on the tensor cores
+    // (mixed modes without the FP64 master store)
+    bool tc_store() const { return nsplit > 0 && !opt.fp64_store; }
+    // the operator store has an FP64 copy (FP64 mode, or mixed with fp64_store)
+    bool f64_store() const { return nsplit == 0 || opt.fp64_store; }
     // the `lo` array of a piece buffer holds piece 1, then (three pieces) piece 2
     int lo_pieces() const { return nsplit == 3 ? 2 : 1; }
     cudaStream_t stream = nullptr;
