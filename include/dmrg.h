@@ -216,6 +216,49 @@ const char* dmrg_last_error(dmrg_plan_t plan);
 void dmrg_destroy(dmrg_plan_t plan);
 
 /* ------------------------------------------------------------------------
+ * Learned Davidson preconditioner (DMRG_PRECOND_MLP).  Not in the paper.
+ * A per-element MLP g(x), 5 -> 64 -> 64 -> 1 with tanh, scales the diagonal
+ * correction: t_i = -g_i r_i / (H_ii - theta).  Inputs of element i:
+ * ((H_ii - theta)/s, theta/s, r_i/|r|_inf, N_L/N, 2Sz_L/N), s = max|H_ii - theta|.
+ * FP32 parameters (Adam), bf16 weights in the Davidson inference.  Until it is
+ * trained (or when an output is not finite) Davidson uses the Jacobi step and
+ * counts the fallback in dmrg_stats_t.precond_fallbacks.
+ * ------------------------------------------------------------------------ */
+
+/* Seeded initialisation (g = 1, i.e. the Jacobi step); clears "trained". */
+dmrg_status dmrg_mlp_init(dmrg_plan_t plan, uint32_t seed);
+
+/* Runs plain (Jacobi) Davidson at the current bond from psi_dev (updated to
+ * the Ritz vector); at every iteration the Jacobi-Davidson correction
+ * equation of root 0 is solved by MINRES (jd_iters iterations at most), and
+ * up to per_solve strided elements give training pairs (features, target
+ * g_i = -t_i (H_ii - theta)/r_i, clipped to [-10, 10]) appended to the plan's
+ * training set.  *n_pairs receives the number added. */
+dmrg_status dmrg_mlp_harvest(dmrg_plan_t plan, double* psi_dev, int max_iter, int jd_iters, int64_t per_solve,
+                             double* energy, int64_t* n_pairs, void* stream);
+
+/* steps Adam steps (learning rate lr) on batches of `batch` pairs drawn from
+ * the training set by a seeded counter-based generator; loss (mean squared
+ * error of g) of the first and last batch.  Marks the network trained. */
+dmrg_status dmrg_mlp_train(dmrg_plan_t plan, int steps, int64_t batch, float lr, uint64_t seed,
+                           float* loss_first, float* loss_last, void* stream);
+
+/* g_dev[i] = g(x_dev[5i .. 5i+4]) for n rows (device FP32); bf16 selects the
+ * inference weights. */
+dmrg_status dmrg_mlp_eval(dmrg_plan_t plan, const float* x_dev, int64_t n, float* g_dev, int bf16, void* stream);
+
+/* Gradient of (1/n) sum_i (g(x_i) - y_i)^2 with respect to the parameters
+ * (layout of dmrg_mlp_params) into grad_dev, the loss into loss_dev (device). */
+dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x_dev, const float* y_dev, int64_t n,
+                              float* grad_dev, float* loss_dev, void* stream);
+
+/* Parameters (host, dmrg_mlp_num_params() floats: W1[64x5], b1[64],
+ * W2[64x64], b2[64], W3[64], b3): get (set = 0) or set (set = 1; marks the
+ * network trained). */
+dmrg_status dmrg_mlp_params(dmrg_plan_t plan, float* host, int set);
+int dmrg_mlp_num_params(void);
+
+/* ------------------------------------------------------------------------
  * Kernel-level entry point used by the unit tests (the same grouped GEMM
  * engine that runs every sigma, renormalisation and intermediate product).
  * Computes, for each of n_out output blocks o (host arrays of n_out):

@@ -79,6 +79,14 @@ _SIGS = {
     "dmrg_grouped_gemm_noalloc": (C.c_int, [C.c_int, _I, _I, _L, _I, _I, _L, _I, _I, _L, _I, _I, _D,
                                             _P, _P, _P, _P]),
     "dmrg_noalloc_scratch_bytes": (C.c_int64, []),
+    "dmrg_mlp_init": (C.c_int, [_P, C.c_uint32]),
+    "dmrg_mlp_harvest": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _D, _L, _P]),
+    "dmrg_mlp_train": (C.c_int, [_P, C.c_int, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_float),
+                                 C.POINTER(C.c_float), _P]),
+    "dmrg_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
+    "dmrg_mlp_gradient": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "dmrg_mlp_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
+    "dmrg_mlp_num_params": (C.c_int, []),
 }
 
 
@@ -241,6 +249,46 @@ class Plan:
         s = Stats()
         self._call("dmrg_stats", C.byref(s))
         return s.as_dict()
+
+    # --- learned Davidson preconditioner -----------------------------------
+    def mlp_init(self, seed=3):
+        self._call("dmrg_mlp_init", int(seed))
+
+    def mlp_harvest(self, psi, max_iter=40, jd_iters=40, per_solve=1 << 14, stream=None):
+        """Plain Davidson at the current bond collecting Jacobi-Davidson pairs;
+        returns (energy, pairs added)."""
+        e = C.c_double(0.0)
+        n = C.c_int64(0)
+        self._call("dmrg_mlp_harvest", _ptr(psi), int(max_iter), int(jd_iters), int(per_solve), C.byref(e),
+                   C.byref(n), _stream(stream))
+        return e.value, n.value
+
+    def mlp_train(self, steps=400, batch=4096, lr=3e-3, seed=3, stream=None):
+        """Adam on the collected pairs; returns (first, last) batch loss."""
+        l0, l1 = C.c_float(0.0), C.c_float(0.0)
+        self._call("dmrg_mlp_train", int(steps), int(batch), float(lr), int(seed), C.byref(l0), C.byref(l1),
+                   _stream(stream))
+        return l0.value, l1.value
+
+    def mlp_eval(self, x, g, bf16=False, stream=None):
+        """g[i] = MLP(x[i, :5]) for device FP32 tensors."""
+        n = int(x.numel() // 5)
+        self._call("dmrg_mlp_eval", _ptr(x), n, _ptr(g), int(bool(bf16)), _stream(stream))
+
+    def mlp_gradient(self, x, y, grad, loss, stream=None):
+        n = int(x.numel() // 5)
+        self._call("dmrg_mlp_gradient", _ptr(x), _ptr(y), n, _ptr(grad), _ptr(loss), _stream(stream))
+
+    def mlp_params(self, values=None):
+        """Get (values None) or set the FP32 parameters (numpy float32 array)."""
+        n = int(lib().dmrg_mlp_num_params())
+        if values is None:
+            out = np.zeros(n, dtype=np.float32)
+            self._call("dmrg_mlp_params", out.ctypes.data_as(C.POINTER(C.c_float)), 0)
+            return out
+        arr = np.ascontiguousarray(values, dtype=np.float32)
+        assert arr.size == n
+        self._call("dmrg_mlp_params", arr.ctypes.data_as(C.POINTER(C.c_float)), 1)
 
 
 def grouped_gemm(precision, blocks, a, b, c, stream=None):

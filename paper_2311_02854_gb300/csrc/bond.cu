@@ -825,6 +825,28 @@ void set_bond(Plan& P, int k) {
         hl.chunks.emplace_back(WorkList(), std::move(w));
         hl.upload(P.stream);
     }
+    // per-sector quantum numbers of the left block (features of the learned preconditioner)
+    {
+        std::vector<int64_t> off(P.layout.size() + 1, 0);
+        std::vector<float> q(2 * std::max<size_t>(P.layout.size(), 1), 0.f);
+        const auto& bl = P.mps.bonds[k - 1];
+        for (size_t i = 0; i < P.layout.size(); ++i) {
+            off[i] = P.layout[i].off;
+            q[2 * i] = (float)bl[P.layout[i].il][0] / (float)std::max(P.N, 1);
+            q[2 * i + 1] = (float)bl[P.layout[i].il][1] / (float)std::max(P.N, 1);
+        }
+        off[P.layout.size()] = P.dim;
+        Mlp& m = P.mlp;
+        cudaFree(m.d_sec_off);
+        cudaFree(m.d_sec_q);
+        m.n_sec = (int)std::max<size_t>(P.layout.size(), 1);
+        DMRG_CHECK_CUDA(cudaMalloc(&m.d_sec_off, off.size() * sizeof(int64_t)));
+        DMRG_CHECK_CUDA(cudaMalloc(&m.d_sec_q, q.size() * sizeof(float)));
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(m.d_sec_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                        P.stream));
+        DMRG_CHECK_CUDA(
+            cudaMemcpyAsync(m.d_sec_q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+    }
     P.stats.ms_host_plan += host_ms_since(hs0);
     P.bond = k;
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));

@@ -350,6 +350,107 @@ dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi, int n_roots, double tol
     });
 }
 
+dmrg_status dmrg_mlp_init(dmrg_plan_t plan, uint32_t seed) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    return guarded(plan, [&]() {
+        Plan& P = plan->P;
+        mlp_init(P.mlp, seed, P.stream);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+        P.mlp.trained = false;
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_mlp_harvest(dmrg_plan_t plan, double* psi, int max_iter, int jd_iters, int64_t per_solve,
+                             double* energy, int64_t* n_pairs, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || max_iter < 1 || jd_iters < 1 || per_solve < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        pick(plan, stream);
+        Plan& P = plan->P;
+        if (!P.mlp.d_w) mlp_init(P.mlp, 3u, P.stream);
+        P.harvest.on = true;
+        P.harvest.jd_iters = jd_iters;
+        P.harvest.per_solve = per_solve;
+        const int64_t before = P.harvest.pairs;
+        double e = 0.0;
+        int it = 0;
+        dmrg_status st = DMRG_OK;
+        try {
+            st = davidson(P, psi, 1, P.opt.tol, max_iter, DMRG_PRECOND_JACOBI, &e, &it);
+        } catch (...) {
+            P.harvest.on = false;
+            throw;
+        }
+        P.harvest.on = false;
+        if (energy) *energy = e;
+        if (n_pairs) *n_pairs = P.harvest.pairs - before;
+        return st == DMRG_ENOTCONV ? DMRG_OK : st;
+    });
+}
+
+dmrg_status dmrg_mlp_train(dmrg_plan_t plan, int steps, int64_t batch, float lr, uint64_t seed, float* loss_first,
+                           float* loss_last, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (steps < 1 || batch < 1 || !(lr > 0.f)) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        if (!P.mlp.d_w) mlp_init(P.mlp, 3u, st);
+        mlp_train(P.mlp, steps, batch, lr, seed, loss_first, loss_last, st);
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_mlp_eval(dmrg_plan_t plan, const float* x, int64_t n, float* g, int bf16, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!x || !g || n < 0) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        DMRG_REQUIRE(P.mlp.d_w, DMRG_EINVAL, "MLP not initialised (dmrg_mlp_init)");
+        mlp_forward(P.mlp, x, n, g, bf16 != 0, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x, const float* y, int64_t n, float* grad, float* loss,
+                              void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!x || !y || !grad || !loss || n < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        DMRG_REQUIRE(P.mlp.d_w, DMRG_EINVAL, "MLP not initialised (dmrg_mlp_init)");
+        mlp_gradient(P.mlp, x, y, n, grad, loss, st);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_mlp_params(dmrg_plan_t plan, float* host, int set) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!host) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        Plan& P = plan->P;
+        if (!P.mlp.d_w) mlp_init(P.mlp, 3u, P.stream);
+        if (set) {
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(P.mlp.d_w, host, kMlpParams * sizeof(float), cudaMemcpyHostToDevice,
+                                            P.stream));
+            mlp_publish(P.mlp, P.stream);
+            P.mlp.trained = true;
+        } else {
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(host, P.mlp.d_w, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost,
+                                            P.stream));
+        }
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+        return DMRG_OK;
+    });
+}
+
+int dmrg_mlp_num_params(void) { return kMlpParams; }
+
 dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi, int n_roots, int D, int forward, double* discarded,
                           double* next_psi, int64_t* next_dim, void* stream) {
     if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");

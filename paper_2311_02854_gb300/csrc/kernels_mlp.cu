@@ -223,6 +223,20 @@ uint64_t mix64_host(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+__global__ void absmax_kernel(const double* __restrict__ x, double shift, int64_t n, double* __restrict__ part) {
+    __shared__ double red[256];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[i] - shift));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
 int grid_n(int64_t n) {
     int64_t g = (n + NT - 1) / NT;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
@@ -339,6 +353,19 @@ void mlp_publish(Mlp& m, cudaStream_t st) {
     to_bf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m.d_w, m.d_wb, kMlpParams);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
+}
+
+double dev_absmax(const double* x, double shift, int64_t n, double* work, cudaStream_t st) {
+    if (n <= 0) return 0.0;
+    const int blocks = (int)std::min<int64_t>(512, (n + 255) / 256);
+    absmax_kernel<<<blocks, 256, 0, st>>>(x, shift, n, work);
+    ++launch_counter();
+    std::vector<double> h(blocks);
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(h.data(), work, blocks * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    double m = 0.0;
+    for (double v : h) m = std::max(m, v);
+    return m;
 }
 
 void mlp_apply(const double* r, const double* hd, double theta, const float* g, double* t, int64_t n,

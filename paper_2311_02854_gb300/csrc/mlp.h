@@ -65,6 +65,9 @@ void mlp_apply(const double* r, const double* hd, double theta, const float* g, 
 int64_t mlp_collect(Mlp& m, const double* hd, const double* r, const double* t, double theta, double s, double rmax,
                     int64_t n, int64_t max_take, cudaStream_t st);
 
+// max_i |x_i - shift| (host result; work holds >= 512 doubles)
+double dev_absmax(const double* x, double shift, int64_t n, double* work, cudaStream_t st);
+
 // steps Adam steps on batches of B pairs drawn (counter-based, seeded) from the
 // training set; loss of the first and last batch to the host; publishes the
 // bf16 weights and marks the network trained

@@ -210,6 +210,8 @@ Plan::~Plan() {
     free_bf16(w_hi, n_wpc);
     free_lo(w_lo, n_wpc);
     if (d_psi_jobs) cudaFree(d_psi_jobs);
+    mlp.release();
+    if (d_mlp_feat) cudaFree(d_mlp_feat);
     if (d_ctr) cudaFree(d_ctr);
     sigma_tc.release();
     free(interm.d, interm.n);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "mlp.h"
 #include "tc.h"
 #include "symbolic.h"
 
@@ -173,6 +174,17 @@ struct Plan {
     // Davidson workspace
     double* d_dav = nullptr;
     int64_t n_dav = 0;
+    // learned preconditioner and the harvesting of its training pairs
+    Mlp mlp;
+    float* d_mlp_feat = nullptr;  // features (5 per element) and outputs of the current bond
+    int64_t n_mlp_feat = 0;
+    struct Harvest {
+        bool on = false;
+        int jd_iters = 40;        // MINRES iterations per correction equation
+        double jd_tol = 1e-8;     // relative residual of the correction equation
+        int64_t per_solve = 1 << 14;
+        int64_t pairs = 0;
+    } harvest;
 
     double* alloc(int64_t n);
     void free(double*& p, int64_t n);

@@ -8,6 +8,7 @@
 
 #include "bond.h"
 #include "eig.h"
+#include "mlp.h"
 
 namespace dmrg {
 
@@ -21,6 +22,75 @@ double host_dot(Plan& P, const double* x, const double* y, int64_t n, double* d_
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
     return r;
 }
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Jacobi-Davidson correction equation (training pairs of the learned
+// preconditioner): (I - u u^T)(H - theta)(I - u u^T) t = -r, t orthogonal to u,
+// solved by MINRES (Paige and Saunders, 1975) with the plan's sigma.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int jd_solve(Plan& P, const double* u, double theta, const double* r, double* t, int max_it, double tol,
+             double* dco, double* dwork) {
+    const int64_t n = P.dim;
+    cudaStream_t st = P.stream;
+    double* buf = P.alloc(7 * n);
+    double *r1 = buf, *r2 = buf + n, *y = buf + 2 * n, *v = buf + 3 * n, *w = buf + 4 * n, *w1 = buf + 5 * n,
+           *w2 = buf + 6 * n;
+    auto dot = [&](const double* a, const double* b) { return host_dot(P, a, b, n, dco, dwork); };
+    // b = -r
+    dev_axpby(-1.0, r, 0.0, r1, n, st);
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(r2, r1, n * 8, cudaMemcpyDeviceToDevice, st));
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(y, r1, n * 8, cudaMemcpyDeviceToDevice, st));
+    dev_fill(t, 0.0, n, st);
+    dev_fill(w, 0.0, n, st);
+    dev_fill(w1, 0.0, n, st);
+    dev_fill(w2, 0.0, n, st);
+    const double beta1 = std::sqrt(std::max(0.0, dot(r1, r1)));
+    int it = 0;
+    if (beta1 > 0.0) {
+        double oldb = 0.0, beta = beta1, dbar = 0.0, epsln = 0.0, phibar = beta1, cs = -1.0, sn = 0.0;
+        for (it = 1; it <= max_it; ++it) {
+            dev_axpby(1.0 / beta, y, 0.0, v, n, st);
+            // y = (I - u u^T)(H - theta) v
+            sigma(P, v, y, 1, st);
+            dev_axpby(-theta, v, 1.0, y, n, st);
+            const double uy = dot(u, y);
+            dev_axpby(-uy, u, 1.0, y, n, st);
+            if (it >= 2) dev_axpby(-beta / oldb, r1, 1.0, y, n, st);
+            const double alfa = dot(v, y);
+            dev_axpby(-alfa / beta, r2, 1.0, y, n, st);
+            std::swap(r1, r2);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(r2, y, n * 8, cudaMemcpyDeviceToDevice, st));
+            oldb = beta;
+            beta = std::sqrt(std::max(0.0, dot(r2, r2)));
+            const double oldeps = epsln;
+            const double delta = cs * dbar + sn * alfa;
+            const double gbar = sn * dbar - cs * alfa;
+            epsln = sn * beta;
+            dbar = -cs * beta;
+            const double gamma = std::max(std::sqrt(gbar * gbar + beta * beta), 1e-300);
+            cs = gbar / gamma;
+            sn = beta / gamma;
+            const double phi = cs * phibar;
+            phibar = sn * phibar;
+            // w = (v - oldeps w1 - delta w2) / gamma with (w1, w2) <- (w2, w)
+            std::swap(w1, w2);
+            std::swap(w2, w);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(w, v, n * 8, cudaMemcpyDeviceToDevice, st));
+            dev_axpby(-oldeps, w1, 1.0, w, n, st);
+            dev_axpby(-delta, w2, 1.0, w, n, st);
+            dev_axpby(0.0, w, 1.0 / gamma, w, n, st);
+            dev_axpby(phi, w, 1.0, t, n, st);
+            if (!(phibar == phibar) || phibar <= tol * beta1 || beta <= 1e-300) break;
+        }
+    }
+    P.free(buf, 7 * n);
+    return it;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -176,12 +246,37 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             break;
         }
         if (it >= max_iter) break;
-        // corrections
+        // training pairs: the plain method's converged correction for root 0
+        if (P.harvest.on) {
+            double* tjd = P.alloc(n);
+            jd_solve(P, X, theta[0], T, tjd, P.harvest.jd_iters, P.harvest.jd_tol, dco, dwork);
+            const double s_ = dev_absmax(hd, theta[0], n, dwork, st);
+            const double rmax = dev_absmax(T, 0.0, n, dwork, st);
+            P.harvest.pairs += mlp_collect(P.mlp, hd, T, tjd, theta[0], s_, rmax, n, P.harvest.per_solve, st);
+            P.free(tjd, n);
+        }
+        // corrections: diagonal (Jacobi), or scaled per element by the learned g
+        const bool use_mlp = precond == DMRG_PRECOND_MLP && P.mlp.trained && !P.harvest.on;
+        if (use_mlp && P.n_mlp_feat < 6 * n) {
+            if (P.d_mlp_feat) cudaFree(P.d_mlp_feat);
+            P.n_mlp_feat = 6 * n;
+            DMRG_CHECK_CUDA(cudaMalloc(&P.d_mlp_feat, P.n_mlp_feat * sizeof(float)));
+        }
         for (int i = 0; i < nr; ++i) {
             double* ri = T + (int64_t)i * n;
-            dev_jacobi_precond(ri, hd, theta[i], ri, n, st);
+            if (use_mlp) {
+                float* xf = P.d_mlp_feat;
+                float* gf = P.d_mlp_feat + 5 * n;
+                const double s_ = dev_absmax(hd, theta[i], n, dwork, st);
+                const double rmax = dev_absmax(ri, 0.0, n, dwork, st);
+                mlp_features(P.mlp, hd, ri, theta[i], s_, rmax, n, xf, st);
+                mlp_forward(P.mlp, xf, n, gf, true, st);
+                mlp_apply(ri, hd, theta[i], gf, ri, n, st);
+            } else {
+                dev_jacobi_precond(ri, hd, theta[i], ri, n, st);
+            }
         }
-        if (precond == DMRG_PRECOND_MLP) P.stats.precond_fallbacks += nr;
+        if (precond == DMRG_PRECOND_MLP && !use_mlp) P.stats.precond_fallbacks += nr;
         nnew = nr;
         if (m + nr > ms) {  // restart with the Ritz vectors
             DMRG_CHECK_CUDA(cudaMemcpyAsync(V, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
