@@ -418,60 +418,63 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
 
     const auto host0 = std::chrono::steady_clock::now();
     ProductList pl;
-    std::map<std::pair<int, int>, int> outidx;  // (target, pair) -> out block
-    auto site_view = [&](int il, int n, int ir, bool tr) {
-        View v;
-        auto it = A.off.find({il, n, ir});
-        v.buf = BUF_PSI;
-        v.off = it->second.first;
-        v.ld = it->second.second;
-        v.tr = tr;
-        return v;
-    };
     std::vector<std::array<int, 3>> keys;
     for (auto& kv : P.mps.sites[m]) keys.push_back(kv.first);
     const auto& bl = P.mps.bonds[m - 1];
     const auto& br = P.mps.bonds[m];
-    // bra lookup: forward (jl, c') -> jr ; backward (n', jr) -> jl
-    std::map<std::pair<int, int>, int> fwd_bra, bwd_bra;
+    const int nl = (int)bl.size(), nrb = (int)br.size();
+    // dense tables: site block (il, n, ir) -> (offset, ld); bra lookups
+    // forward (jl, c') -> jr and backward (n', jr) -> jl
+    std::vector<std::pair<int64_t, int>> site_at((size_t)nl * 4 * nrb, {-1, 0});
+    std::vector<int> fwd_bra((size_t)nl * 4, -1), bwd_bra((size_t)4 * nrb, -1);
     for (auto& kk : keys) {
-        fwd_bra[{kk[0], kk[1]}] = kk[2];
-        bwd_bra[{kk[1], kk[2]}] = kk[0];
+        site_at[((size_t)kk[0] * 4 + kk[1]) * nrb + kk[2]] = A.off[kk];
+        fwd_bra[(size_t)kk[0] * 4 + kk[1]] = kk[2];
+        bwd_bra[(size_t)kk[1] * nrb + kk[2]] = kk[0];
     }
+    auto site_view = [&](int il, int n, int ir, bool tr) {
+        View v;
+        const auto& at = site_at[((size_t)il * 4 + n) * nrb + ir];
+        v.buf = BUF_PSI;
+        v.off = at.first;
+        v.ld = at.second;
+        v.tr = tr;
+        return v;
+    };
+    const int nxb = XL.basis.size();
+    std::vector<OpLookup> xcache(nxb);
+    std::vector<int> out_of_pair;
     for (int t = 0; t < (int)rp.targets.size(); ++t) {
         const RenormTarget& T = rp.targets[t];
         auto fr = OL.find(T.key);
         const Family& of = OL.fams[fr.first];
         const int64_t obase = of.base + (int64_t)fr.second * of.stride;
+        out_of_pair.assign(of.bra.size(), -1);  // pair of the target -> output block
         for (const Term2& term : T.terms) {
             const LocalOp& M = rp.site.ops[term.site];
             const int parX = ref_parity(XL, rp.interms, term.X);
+            for (int i = 0; i < nxb; ++i) xcache[i] = lookup(XL, rp.interms, term.X, i, BUF_L);
             for (auto& kk : keys) {
                 const int il = kk[0], n = kk[1], ir = kk[2];
                 if (forward) {
                     // ket component (il, n) of X.C -> new sector ir; X acts on il
-                    OpLookup ox = lookup(XL, rp.interms, term.X, il, BUF_L);
+                    const OpLookup& ox = xcache[il];
                     if (!ox.ok) continue;
                     const int jl = ox.j;
                     for (int c2 = 0; c2 < 4; ++c2) {
                         const double mv = M.at(c2, n);
                         if (mv == 0.0) continue;
-                        auto bj = fwd_bra.find({jl, c2});
-                        if (bj == fwd_bra.end()) continue;
-                        const int jr = bj->second;
+                        const int jr = fwd_bra[(size_t)jl * 4 + c2];
+                        if (jr < 0) continue;
                         const int pr = of.pair_of_ket[ir];
                         if (pr < 0 || of.bra[pr] != jr) continue;
                         const int dl = bl[il][2], djl = bl[jl][2], dr = br[ir][2], djr = br[jr][2];
                         const double zeta = (M.parity && (XL.basis.qn[il].n & 1)) ? -1.0 : 1.0;
-                        auto key = std::make_pair(t, pr);
-                        auto oi = outidx.find(key);
-                        int o;
-                        if (oi == outidx.end()) {
+                        int o = out_of_pair[pr];
+                        if (o < 0) {
                             o = (int)pl.outs.size();
-                            outidx[key] = o;
+                            out_of_pair[pr] = o;
                             pl.outs.push_back({BUF_R, obase + of.off[pr], djr, dr, of.ld[pr]});
-                        } else {
-                            o = oi->second;
                         }
                         Contrib c;
                         c.out = o;
@@ -487,28 +490,23 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
                     }
                 } else {
                     // ket component (n, ir) of C.X -> new sector il; X acts on ir
-                    OpLookup ox = lookup(XL, rp.interms, term.X, ir, BUF_L);
+                    const OpLookup& ox = xcache[ir];
                     if (!ox.ok) continue;
                     const int jr = ox.j;
                     for (int n2 = 0; n2 < 4; ++n2) {
                         const double mv = M.at(n2, n);
                         if (mv == 0.0) continue;
-                        auto bj = bwd_bra.find({n2, jr});
-                        if (bj == bwd_bra.end()) continue;
-                        const int jl = bj->second;
+                        const int jl = bwd_bra[(size_t)n2 * nrb + jr];
+                        if (jl < 0) continue;
                         const int pr = of.pair_of_ket[il];
                         if (pr < 0 || of.bra[pr] != jl) continue;
                         const int dl = bl[il][2], djl = bl[jl][2], dr = br[ir][2], djr = br[jr][2];
                         const double zeta = (parX && (kSiteQN[n].n & 1)) ? -1.0 : 1.0;
-                        auto key = std::make_pair(t, pr);
-                        auto oi = outidx.find(key);
-                        int o;
-                        if (oi == outidx.end()) {
+                        int o = out_of_pair[pr];
+                        if (o < 0) {
                             o = (int)pl.outs.size();
-                            outidx[key] = o;
+                            out_of_pair[pr] = o;
                             pl.outs.push_back({BUF_R, obase + of.off[pr], djl, dl, of.ld[pr]});
-                        } else {
-                            o = oi->second;
                         }
                         Contrib c;
                         c.out = o;
@@ -614,6 +612,7 @@ void ensure_env(Plan& P, int k) {
 void build_layout(Plan& P, int k) {
     P.layout.clear();
     P.sector_of.clear();
+    P.sector_idx.assign(16 * std::max<size_t>(P.mps.bonds[k - 1].size(), 1), -1);
     const auto& bl = P.mps.bonds[k - 1];
     const auto& br = P.mps.bonds[k + 1];
     std::map<std::pair<int, int>, int> ridx;
@@ -626,6 +625,7 @@ void build_layout(Plan& P, int k) {
             if (it == ridx.end()) continue;
             Plan::Sector s{il, y, it->second, off, bl[il][2], br[it->second][2], poff};
             P.sector_of[{il, y}] = (int)P.layout.size();
+            P.sector_idx[16 * il + y] = (int)P.layout.size();
             P.layout.push_back(s);
             off += (int64_t)s.dl * s.dr;
             poff += (int64_t)s.dl * round_up(s.dr, 8);
@@ -669,28 +669,33 @@ void set_bond(Plan& P, int k) {
     for (const Plan::Sector& s : P.layout) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
     const LocalOps& Y = P.sp.y;
     int64_t nitems = 0;
+    // the blocks of a term's operators depend only on the ket sector of their side
+    const int nbl = L.lay.basis.size(), nbr = R.lay.basis.size();
+    std::vector<OpLookup> lcache(nbl), rcache(nbr);
     for (const Term3& t : P.sp.terms) {
         const LocalOp& M = Y.ops[t.y];
         const int pR = ref_parity(R.lay, P.sp.interms, t.R);
+        for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
+        for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
         for (size_t si = 0; si < P.layout.size(); ++si) {
             const Plan::Sector& s = P.layout[si];
-            OpLookup ol = lookup(L.lay, P.sp.interms, t.L, s.il, BUF_L);
+            const OpLookup& ol = lcache[s.il];
             if (!ol.ok) continue;
-            OpLookup orr = lookup(R.lay, P.sp.interms, t.R, s.ir, BUF_R);
+            const OpLookup& orr = rcache[s.ir];
             if (!orr.ok) continue;
             const int nl = L.lay.basis.qn[s.il].n;
             const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
             for (int y2 = 0; y2 < 16; ++y2) {
                 const double mv = M.at(y2, s.y);
                 if (mv == 0.0) continue;
-                auto it = P.sector_of.find({ol.j, y2});
-                if (it == P.sector_of.end()) continue;
-                const Plan::Sector& o = P.layout[it->second];
+                const int os = P.sector_idx[16 * ol.j + y2];
+                if (os < 0) continue;
+                const Plan::Sector& o = P.layout[os];
                 DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
                 const int e = M.parity * nl + pR * (nl + ny);
                 const double zeta = (e & 1) ? -1.0 : 1.0;
                 Contrib c;
-                c.out = it->second;
+                c.out = os;
                 c.P = ol.v;  // O^L_eff : d_jl x d_il
                 c.Q.buf = BUF_PSI;
                 c.Q.off = s.off;
@@ -780,13 +785,15 @@ void set_bond(Plan& P, int k) {
             const LocalOp& M = Y.ops[t.y];
             if (M.dq != QN(0, 0)) continue;
             const int pR = ref_parity(R.lay, P.sp.interms, t.R);
+            for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
+            for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
             for (size_t si = 0; si < P.layout.size(); ++si) {
                 const Plan::Sector& s = P.layout[si];
                 const double mv = M.at(s.y, s.y);
                 if (mv == 0.0) continue;
-                OpLookup ol = lookup(L.lay, P.sp.interms, t.L, s.il, BUF_L);
+                const OpLookup& ol = lcache[s.il];
                 if (!ol.ok || ol.j != s.il) continue;
-                OpLookup orr = lookup(R.lay, P.sp.interms, t.R, s.ir, BUF_R);
+                const OpLookup& orr = rcache[s.ir];
                 if (!orr.ok || orr.j != s.ir) continue;
                 const int nl = L.lay.basis.qn[s.il].n;
                 const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;

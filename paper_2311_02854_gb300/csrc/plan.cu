@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <fstream>
+#include <unordered_map>
 
 #include "plan.h"
 
@@ -285,7 +286,8 @@ void ProductList::lower(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t
     };
     while (i < cs.size()) {
         WorkList p1, p2;
-        std::map<int, std::vector<Seg>> segs;
+        std::vector<std::vector<Seg>> segs(outs.size());
+        std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;
         int64_t used = 0;
         for (; i < cs.size(); ++i) {
@@ -302,7 +304,10 @@ void ProductList::lower(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t
                 if (used + need > cap && used > 0) break;
                 flops += std::min(cost_pq, cost_qr);
             }
-            if (!segs.count(c.out)) order.push_back(c.out);
+            if (!seen[c.out]) {
+                seen[c.out] = 1;
+                order.push_back(c.out);
+            }
             std::vector<Seg>& sv = segs[c.out];
             if (nreal == 3) {
                 View T;
@@ -356,7 +361,8 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
     size_t i = 0;
     while (i < cs.size()) {
         WorkList p1, p2;
-        std::map<int, std::vector<Seg>> segs;
+        std::vector<std::vector<Seg>> segs(outs.size());
+        std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;
         int64_t used = 0;
         for (; i < cs.size(); ++i) {
@@ -381,7 +387,10 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
             }
             if (tr > 0) need = (int64_t)tr * round_up(tc_, 8);
             if (used + need > cap && used > 0) break;
-            if (!segs.count(c.out)) order.push_back(c.out);
+            if (!seen[c.out]) {
+                seen[c.out] = 1;
+                order.push_back(c.out);
+            }
             std::vector<Seg>& sv = segs[c.out];
             View T;
             T.buf = sbuf;
@@ -521,7 +530,7 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
     while (i < cs.size()) {
         // pass 1: the items of this chunk, their phase-1 shapes and scratch groups
         std::vector<Item> items;
-        std::map<std::pair<int, int>, int> gidx;
+        std::unordered_map<int64_t, int> gidx;  // (rows << 32 | cols) -> scratch group
         std::vector<std::array<int64_t, 4>> groups;  // rows, cols, count, base
         int64_t used = 0;
         size_t j = i;
@@ -569,7 +578,7 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
             if (it.kind >= 2) need = (int64_t)it.tr * round_up(it.tcl, 8);
             if (used + need > cap && used > 0) break;
             if (it.kind >= 2) {
-                auto key = std::make_pair(it.tr, it.tcl);
+                const int64_t key = ((int64_t)it.tr << 32) | (int64_t)it.tcl;
                 auto g = gidx.find(key);
                 if (g == gidx.end()) {
                     g = gidx.emplace(key, (int)groups.size()).first;
@@ -588,12 +597,16 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         }
         // pass 2: work lists
         TmaWorkList p1, p2;
-        std::map<int, std::vector<TSeg>> segs;
+        std::vector<std::vector<TSeg>> segs(outs.size());
+        std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;
         for (size_t q = 0; q < items.size(); ++q) {
             const Contrib& c = cs[i + q];
             const Item& it = items[q];
-            if (!segs.count(c.out)) order.push_back(c.out);
+            if (!seen[c.out]) {
+                seen[c.out] = 1;
+                order.push_back(c.out);
+            }
             std::vector<TSeg>& sv = segs[c.out];
             View T;
             if (it.kind >= 2) {

@@ -138,6 +138,7 @@ struct Plan {
     };
     std::vector<Sector> layout;
     std::map<std::pair<int, int>, int> sector_of;  // (il, y) -> sector
+    std::vector<int> sector_idx;                    // dense: il * 16 + y -> sector or -1
     int64_t dim = 0, dim_pad = 0;
     SigmaPlan sp;
     IntermStore interm;  // the bond's intermediates

@@ -6,6 +6,7 @@
 
 #include <map>
 #include <tuple>
+#include <unordered_map>
 
 #include "engine.h"
 
@@ -85,9 +86,24 @@ struct MapKey {
     bool operator<(const MapKey& o) const { return tie() < o.tie(); }
 };
 
+struct MapKeyHash {
+    size_t operator()(const MapKey& k) const {
+        uint64_t h = 0x9e3779b97f4a7c15ull ^ (uint64_t)k.buf;
+        const int64_t v[9] = {k.off, k.cols, k.rows, k.ld, k.nz, k.zstride, k.nv, k.vstride, 0};
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint64_t)v[i] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+            h *= 0xff51afd7ed558ccdull;
+        }
+        return (size_t)(h ^ (h >> 33));
+    }
+};
+struct MapKeyEq {
+    bool operator()(const MapKey& a, const MapKey& b) const { return a.tie() == b.tie(); }
+};
+
 struct MapTable {
     std::vector<MapKey> keys;
-    std::map<MapKey, int> index;
+    std::unordered_map<MapKey, int, MapKeyHash, MapKeyEq> index;
     CUtensorMap* d_maps = nullptr;
     size_t cap = 0;
     const void* enc_ptr[kMaxBufs][3] = {};  // piece pointers the device maps were encoded with
