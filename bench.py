@@ -108,6 +108,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic of one middle-bond sigma call of a workload (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over the tensor-core launches of the call, from an
+# ncu capture of `bench.py --sigma-only`), with the tensor-core K stages of that
+# call.  The traffic of a sigma call in the timed steps is taken in proportion to
+# its stages; it is reported only while the kernel source is the one captured.
+SIGMA_TRAFFIC = {
+    "k73_d3000:bf16x3": dict(bytes=1414.849e9 + 245.783e9, stages=33096283 + 31440895,
+                             kernel_sha256="ae70dee3f2586867a7b4d2a5b466a3847d9ac033eb621b2e6ca8548148962021"),
+}
+
+
+def kernel_sha256():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2311_02854_gb300", "csrc", "kernels_tc.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -262,6 +279,16 @@ def run_mine(args):
     sigma_tflops = sigma_flops / (sig_t / 1e3) / 1e12
     peaks, src = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    # roofline of the dominant kernel from the sigma calls of the timed steps:
+    # their algorithmic FLOPs over their summed device time (CUDA events on the
+    # launching stream around each call)
+    d_ms = s_after["ms_sigma_dev"] - s_before["ms_sigma_dev"]
+    d_n = s_after["sigma_timed"] - s_before["sigma_timed"]
+    achieved = (s_after["sigma_flops_dev"] - s_before["sigma_flops_dev"]) / (d_ms / 1e3) / 1e12 if d_ms > 0 else 0.0
+    traffic = None
+    tr = SIGMA_TRAFFIC.get(f"{args.workload}:{args.precision}")
+    if tr and d_n > 0 and kernel_sha256() == tr["kernel_sha256"]:
+        traffic = int(tr["bytes"] / tr["stages"] * (s_after["sigma_stages_dev"] - s_before["sigma_stages_dev"]) / d_n)
     # end-to-end: the same step with the guess from pinned host memory and the
     # final vector read back every step
     host_in = torch.from_numpy(x.cpu().numpy()).pin_memory()
@@ -297,11 +324,17 @@ def run_mine(args):
         "renorm_ms_total": round(st_end["ms_renorm"], 1),
         "davidson_ms_total": round(st_end["ms_davidson"], 1),
         "decim_ms_total": round(st_end["ms_decim"], 1),
+        "decim_ms_parts": {k: round(v, 1) for k, v in zip(("rho", "eigensolver", "host", "guess"),
+                                                          st_end["ms_decim_parts"])},
+        "decim_sweeps_last": st_end["decim_sweeps_last"],
         "sigma_terms": st_end["n_terms"], "sigma_items": st_end["n_items"],
-        "roofline": {"bound": "tensor", "achieved": round(sigma_tflops, 3), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(sigma_tflops / peak, 4), "traffic": None,
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{src} bf16 sustained",
-                     "kernel": "tc_tma_kernel (one sigma call: phase 1 + phase 2 launches)"},
+                     "kernel": "tc_tma_kernel (unit: one sigma call = ψ split + phase 1 + phase 2 launches; "
+                               f"{d_n} calls in the timed steps, {d_ms / max(d_n, 1):.1f} ms each)",
+                     "traffic_note": "DRAM bytes per sigma call, ncu capture of the middle-bond sigma scaled "
+                                     "by tensor-core stages" if traffic else "kernel changed since the capture"},
         "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": int(host_in.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
         "gpu_launches": int(launches),

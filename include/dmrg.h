@@ -96,6 +96,10 @@ typedef struct {
                                renormalisation; the store then carries no tensor-core
                                accumulation error, and with fp64_final the energies are
                                Rayleigh quotients of the FP64 Hamiltonian); default 0 */
+    int sigma_graph;        /* mixed modes: 1 = each sigma replays a CUDA graph (the split of
+                               psi and the tensor-core launches) captured once per bond and
+                               vector count, with psi / sigma staged through plan buffers;
+                               default 1 */
 } dmrg_options;
 
 typedef struct {
@@ -118,6 +122,14 @@ typedef struct {
     int64_t sigma_stages[2];      /* mixed sigma: 64-deep K stages of phase 1 / phase 2 */
     double sigma_mma_flops;       /* mixed sigma: tensor work of the tiles (one bf16 product) */
     int64_t sigma_maps;           /* mixed sigma: tensor maps of the current bond */
+    double ms_decim_parts[4];     /* decimation: density matrices, eigensolver, host
+                                     selection / new site tensor, next-bond guess (all calls) */
+    int decim_sweeps_last;        /* block-Jacobi sweeps of the last decimation */
+    double ms_sigma_dev;          /* device time of all completed sigma calls (CUDA events on
+                                     the launching stream around each call) */
+    double sigma_flops_dev;       /* algorithmic FLOPs of those calls (all vectors) */
+    int64_t sigma_stages_dev;     /* mixed sigma: tensor-core K stages of those calls */
+    int64_t sigma_timed;          /* number of sigma calls in ms_sigma_dev */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

@@ -855,6 +855,7 @@ void set_bond(Plan& P, int k) {
             cudaMemcpyAsync(m.d_sec_q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, P.stream));
     }
     P.stats.ms_host_plan += host_ms_since(hs0);
+    P.drop_graphs();  // captured for the previous bond's work lists
     P.bond = k;
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
 }
@@ -911,9 +912,30 @@ void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t 
     }
 }
 
+namespace {
+void sigma_body(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
+}
+
 void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
     DMRG_REQUIRE(nvec >= 1, DMRG_EINVAL, "nvec must be >= 1");
+    if (P.sig_pending.size() >= 64) P.collect_sigma_times(false);
+    Plan::SigmaEvents ev{P.take_event(), P.take_event(), P.stats.sigma_flops * nvec,
+                         P.mixed() ? (P.stats.sigma_stages[0] + P.stats.sigma_stages[1]) * nvec : 0};
+    try {
+        DMRG_CHECK_CUDA(cudaEventRecord(ev.a, st));
+        sigma_body(P, psi, out, nvec, st);
+        DMRG_CHECK_CUDA(cudaEventRecord(ev.b, st));
+    } catch (...) {
+        P.ev_pool.push_back(ev.a);
+        P.ev_pool.push_back(ev.b);
+        throw;
+    }
+    P.sig_pending.push_back(ev);
+}
+
+namespace {
+void sigma_body(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
     if (!P.mixed()) {
         const int64_t per = std::max<int64_t>(P.sigma_pl.scratch_elems, 1);
         const int group = (int)std::max<int64_t>(1, std::min<int64_t>(nvec, P.n_scratch / per));
@@ -931,20 +953,72 @@ void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
     ProductList& tl = P.sigma_tc;
     const int G = std::max(1, P.opt.n_roots);
     ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
+    // the work of one launch of nv vectors: psi (nv x dim) -> sigma (nv x dim)
+    auto enqueue = [&](const double* in, double* o, int nv, cudaStream_t s) {
+        for (int v = 0; v < nv; ++v)
+            dev_split_blocks(in + (int64_t)v * P.dim, P.d_psi_jobs, P.n_psi_jobs, P.ps_hi + (int64_t)v * P.dim_pad,
+                             P.ps_lo + (int64_t)v * P.dim_pad, s,
+                             P.nsplit == 3 ? P.ps_lo + P.n_ppc + (int64_t)v * P.dim_pad : nullptr);
+        DMRG_CHECK_CUDA(cudaMemsetAsync(o, 0, (size_t)nv * P.dim * 8, s));
+        tl.run_tma(sigma_bufs(P, P.bond, o), nv, P.nsplit, s);
+    };
+    {
+        const TcBufs tb = sigma_bufs(P, P.bond, nullptr);
+        if (tl.maps.stale(tb)) {
+            tl.maps.encode_upload(tb, P.nsplit, st);
+            P.drop_graphs();
+        }
+    }
+    tc_prepare(P.nsplit);  // kernel attributes, set outside any capture
+    const bool graph = P.opt.sigma_graph != 0;
+    if (graph) {
+        const int64_t need = 2 * (int64_t)G * P.dim;
+        if (need > P.n_sig_io) {
+            P.drop_graphs();
+            if (P.d_sig_io) P.free(P.d_sig_io, P.n_sig_io);
+            P.n_sig_io = need;
+            P.d_sig_io = P.alloc(need);
+        }
+        if (!P.cap_stream) DMRG_CHECK_CUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+    }
     for (int v0 = 0; v0 < nvec; v0 += G) {
         const int nv = std::min(G, nvec - v0);
-        for (int v = 0; v < nv; ++v)
-            dev_split_blocks(psi + (int64_t)(v0 + v) * P.dim, P.d_psi_jobs, P.n_psi_jobs,
-                             P.ps_hi + (int64_t)v * P.dim_pad, P.ps_lo + (int64_t)v * P.dim_pad, st,
-                             P.nsplit == 3 ? P.ps_lo + P.n_ppc + (int64_t)v * P.dim_pad : nullptr);
-        DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v0 * P.dim, 0, (size_t)nv * P.dim * 8, st));
-        const TcBufs tb = sigma_bufs(P, P.bond, out + (int64_t)v0 * P.dim);
-        if (tl.maps.stale(tb)) tl.maps.encode_upload(tb, P.nsplit, st);
-        tl.run_tma(tb, nv, P.nsplit, st);
+        if (!graph) {
+            enqueue(psi + (int64_t)v0 * P.dim, out + (int64_t)v0 * P.dim, nv, st);
+            continue;
+        }
+        double* gin = P.d_sig_io;
+        double* gout = P.d_sig_io + (int64_t)G * P.dim;
+        Plan::SigmaGraph& sg = P.sigma_graphs[nv];
+        if (!sg.exec) {
+            // first use at this bond and vector count: capture on the plan's own stream
+            const int64_t l0 = launch_counter();
+            cudaGraph_t g = nullptr;
+            DMRG_CHECK_CUDA(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                enqueue(gin, gout, nv, P.cap_stream);
+            } catch (...) {
+                cudaStreamEndCapture(P.cap_stream, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            DMRG_CHECK_CUDA(cudaStreamEndCapture(P.cap_stream, &g));
+            DMRG_CHECK_CUDA(cudaGraphInstantiate(&sg.exec, g, 0));
+            cudaGraphDestroy(g);
+            sg.launches = launch_counter() - l0;
+            launch_counter() = l0;
+        }
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(gin, psi + (int64_t)v0 * P.dim, (size_t)nv * P.dim * 8,
+                                        cudaMemcpyDeviceToDevice, st));
+        DMRG_CHECK_CUDA(cudaGraphLaunch(sg.exec, st));
+        launch_counter() += sg.launches;
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(out + (int64_t)v0 * P.dim, gout, (size_t)nv * P.dim * 8,
+                                        cudaMemcpyDeviceToDevice, st));
     }
     P.stats.sigma_calls += nvec;
     P.check_device_error();
 }
+}  // namespace
 
 void hdiag(Plan& P, double* out, cudaStream_t st) {
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");

@@ -152,6 +152,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->verbose = 0;
     o->tc_kchunk = 0;
     o->fp64_store = 0;
+    o->sigma_graph = 1;
 }
 
 const char* dmrg_version(void) {
@@ -487,10 +488,13 @@ dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path) {
 
 dmrg_status dmrg_stats(dmrg_plan_t plan, dmrg_stats_t* out) {
     if (!plan || !out) return fail(plan, DMRG_EINVAL, "bad arguments");
-    plan->P.stats.kernel_launches = launch_counter();
-    plan->P.stats.device_bytes = plan->P.dev_bytes;
-    *out = plan->P.stats;
-    return DMRG_OK;
+    return guarded(plan, [&]() {
+        plan->P.collect_sigma_times(true);
+        plan->P.stats.kernel_launches = launch_counter();
+        plan->P.stats.device_bytes = plan->P.dev_bytes;
+        *out = plan->P.stats;
+        return DMRG_OK;
+    });
 }
 
 const char* dmrg_last_error(dmrg_plan_t plan) {

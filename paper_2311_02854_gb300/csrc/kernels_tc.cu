@@ -544,8 +544,8 @@ __global__ void __launch_bounds__(THREADS3, 1)
         if (lane == 0) {
             uint32_t q = 0;
             for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
-                const int tix = t % ntiles, v = t / ntiles;
-                const Tile T = tiles[tix];
+                const int v = t / ntiles;
+                const Tile T = tiles[t % ntiles];
                 const int nst = T.nst;
                 // a second 64-row (or 64-column) half only when the block extends past the first
                 const int nA = (T.m - T.m0 > 64) ? 2 : 1, nB = (T.n - T.n0 > 64) ? 2 : 1;
@@ -832,6 +832,9 @@ void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, con
 }
 
 void TmaWorkList::upload(cudaStream_t st) {
+    // longest tiles first: CTAs take tiles round-robin, so the short ones fill
+    // in at the end of the launch instead of a few long ones trailing
+    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& a, const Tile& b) { return a.nst > b.nst; });
     if (tiles.size() > cap_tiles) {
         if (d_tiles) cudaFree(d_tiles);
         cap_tiles = tiles.size() + 16;
@@ -941,35 +944,34 @@ void MapTable::release() {
     clear();
 }
 
+void tc_prepare(int nsplit) {
+    static bool done[4] = {false, false, false, false};
+    if (nsplit < 1 || nsplit > 3 || done[nsplit]) return;
+    if (nsplit == 1) {
+        DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<1>::SMEM));
+    } else if (nsplit == 2) {
+        DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<2>::SMEM));
+    } else {
+        DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<3>::SMEM));
+    }
+    done[nsplit] = true;
+}
+
 void launch_seg_gemm_tma(const TmaWorkList& w, const MapTable& maps, const TcBufs& b, int nvec, int nsplit,
                          cudaStream_t st) {
+    tc_prepare(nsplit);
     if (w.tiles.empty()) return;
     const int64_t total = (int64_t)w.tiles.size() * nvec;
     DMRG_REQUIRE(total < (1LL << 31), DMRG_EINVAL, "tensor-core work list too large");
     DMRG_REQUIRE(maps.d_maps != nullptr, DMRG_EINVAL, "tensor maps not uploaded");
     const int grid = (int)std::min<int64_t>(total, tc_num_sms());
     if (nsplit == 3) {
-        static bool attr = false;
-        if (!attr) {
-            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<3>::SMEM));
-            attr = true;
-        }
         tc_tma_kernel<3><<<grid, THREADS3, Cfg3<3>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
                                                         maps.d_maps, b);
     } else if (nsplit == 2) {
-        static bool attr = false;
-        if (!attr) {
-            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<2>::SMEM));
-            attr = true;
-        }
         tc_tma_kernel<2><<<grid, THREADS3, Cfg3<2>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
                                                                maps.d_maps, b);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            DMRG_CHECK_CUDA(cudaFuncSetAttribute(tc_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg3<1>::SMEM));
-            attr = true;
-        }
         tc_tma_kernel<1><<<grid, THREADS3, Cfg3<1>::SMEM, st>>>(w.d_tiles, (int)w.tiles.size(), nvec, w.d_segs,
                                                                maps.d_maps, b);
     }

@@ -189,7 +189,54 @@ void Plan::check_device_error() {
     }
 }
 
+void Plan::drop_graphs() {
+    for (auto& kv : sigma_graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    sigma_graphs.clear();
+}
+
+cudaEvent_t Plan::take_event() {
+    if (!ev_pool.empty()) {
+        cudaEvent_t e = ev_pool.back();
+        ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    DMRG_CHECK_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Plan::collect_sigma_times(bool wait) {
+    size_t keep = 0;
+    for (size_t i = 0; i < sig_pending.size(); ++i) {
+        SigmaEvents& x = sig_pending[i];
+        if (wait) DMRG_CHECK_CUDA(cudaEventSynchronize(x.b));
+        else if (cudaEventQuery(x.b) != cudaSuccess) {
+            sig_pending[keep++] = x;
+            continue;
+        }
+        float ms = 0.f;
+        DMRG_CHECK_CUDA(cudaEventElapsedTime(&ms, x.a, x.b));
+        stats.ms_sigma_dev += ms;
+        stats.sigma_flops_dev += x.flops;
+        stats.sigma_stages_dev += x.stages;
+        ++stats.sigma_timed;
+        ev_pool.push_back(x.a);
+        ev_pool.push_back(x.b);
+    }
+    sig_pending.resize(keep);
+    cudaGetLastError();  // a not-ready query leaves no error behind
+}
+
 Plan::~Plan() {
+    for (auto& x : sig_pending) {
+        cudaEventDestroy(x.a);
+        cudaEventDestroy(x.b);
+    }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (d_sig_io) free(d_sig_io, n_sig_io);
     for (auto& b : left)
         if (b) {
             if (b->d) free(b->d, b->n);

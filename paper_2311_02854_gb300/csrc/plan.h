@@ -165,6 +165,30 @@ struct Plan {
     int* d_ctr = nullptr;  // [0] tile counter, [1] device error word
     bool sigma_fp64_ready = false;
 
+    // CUDA graphs of the mixed sigma, per number of vectors in a launch, for the
+    // current bond; psi / sigma are staged through fixed buffers
+    struct SigmaGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    };
+    std::map<int, SigmaGraph> sigma_graphs;
+    cudaStream_t cap_stream = nullptr;
+    double* d_sig_io = nullptr;  // [G x dim in | G x dim out]
+    int64_t n_sig_io = 0;
+    void drop_graphs();
+
+    // device time of each sigma call: an event pair on the launching stream,
+    // read back (without a wait) once the pair has completed
+    struct SigmaEvents {
+        cudaEvent_t a, b;
+        double flops;
+        int64_t stages;
+    };
+    std::vector<SigmaEvents> sig_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaEvent_t take_event();
+    void collect_sigma_times(bool wait);
+
     // host-buffer entry point
     double* d_io = nullptr;
     int64_t n_io = 0;

@@ -3,6 +3,7 @@
 // (Sec. 2.3, Fig. flowchart).  All vector arithmetic runs on the device in
 // FP64; the host keeps only the small subspace matrix and scalars.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <numeric>
 
@@ -424,7 +425,10 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
     BufTable bt{};
     bt.p[BUF_PSI] = const_cast<double*>(psi);
     bt.p[BUF_OUT] = d_rho;
+    const auto hd0 = std::chrono::steady_clock::now();
     launch_seg_gemm_f64(wl, bt, 1, st);
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    const auto hd1 = std::chrono::steady_clock::now();
     // eigen-decomposition of every rho_q
     std::vector<EigJob> jobs;
     int64_t woff = 0;
@@ -440,8 +444,9 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         jobs.push_back(j);
         DMRG_REQUIRE(g.n <= 16384, DMRG_EINVAL, "density-matrix sector larger than 16384");
     }
-    block_jacobi_eigh(
+    P.stats.decim_sweeps_last = block_jacobi_eigh(
         jobs, 40, 1e-14, st, [&](int64_t n) { return P.alloc(n); }, [&](double* p, int64_t n) { P.free(p, n); });
+    const auto hd2 = std::chrono::steady_clock::now();
     std::vector<double> hw(woff), hv(rho_tot);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hw.data(), d_w, woff * 8, cudaMemcpyDeviceToHost, st));
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hv.data(), d_vec, rho_tot * 8, cudaMemcpyDeviceToHost, st));
@@ -533,6 +538,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         for (int m = k + 1; m <= K; ++m)
             free_block(P, P.left[m]);
     }
+    const auto hd3 = std::chrono::steady_clock::now();
     // guess for the next bond: U^T Psi A[k+2] (forward) or A[k-1] Psi V (backward)
     const int kn = forward ? k + 1 : k - 1;
     const auto nbl = P.mps.bonds[kn - 1];
@@ -688,6 +694,14 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
     P.bond = -1;
     cudaEventRecord(e1, st);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    const auto hd4 = std::chrono::steady_clock::now();
+    auto span = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    P.stats.ms_decim_parts[0] += span(hd0, hd1);  // density matrices
+    P.stats.ms_decim_parts[1] += span(hd1, hd2);  // eigensolver
+    P.stats.ms_decim_parts[2] += span(hd2, hd3);  // selection and new site tensor (host)
+    P.stats.ms_decim_parts[3] += span(hd3, hd4);  // next-bond guess
     float ms_ = 0.f;
     cudaEventElapsedTime(&ms_, e0, e1);
     P.stats.ms_decim += ms_;

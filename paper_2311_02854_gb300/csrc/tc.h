@@ -40,6 +40,8 @@ struct TcBufs {
 void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit, cudaStream_t st);
 
 int tc_num_sms();
+// one-time kernel attributes (dynamic shared memory) of the nsplit kernels
+void tc_prepare(int nsplit);
 
 // ---------------------------------------------------------------------------
 // TMA-staged variant: every operand is addressed through a tensor map.
