@@ -34,6 +34,7 @@ WORKLOADS = {
     "k73_d3000": dict(K=73, N=114, twoS=0, D=3000, n_chol=292, ell=8.0, h_min=-6.0, wn=1.45, ws=1.45),
     "k36_d1000": dict(K=36, N=36, twoS=0, D=1000, n_chol=144, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
     "k24_d500": dict(K=24, N=24, twoS=0, D=500, n_chol=96, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
+    "k54_d2000": dict(K=54, N=54, twoS=0, D=2000, n_chol=216, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
 }
 METRIC = "sigma=H*psi TFLOP/s, s/site at K=73,D=3000; mixed vs FP64 at dE<=1e-6 Eh"
 PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2, "bf16x6": 3}
@@ -114,8 +115,8 @@ class ClockSampler:
 # call.  The traffic of a sigma call in the timed steps is taken in proportion to
 # its stages; it is reported only while the kernel source is the one captured.
 SIGMA_TRAFFIC = {
-    "k73_d3000:bf16x3": dict(bytes=1414.849e9 + 245.783e9, stages=33096283 + 31440895,
-                             kernel_sha256="ae70dee3f2586867a7b4d2a5b466a3847d9ac033eb621b2e6ca8548148962021"),
+    "k73_d3000:bf16x3": dict(bytes=1405.693e9 + 249.750e9, stages=33096283 + 31440895,
+                             kernel_sha256="b9a1c588ded3f8bdc26f7b9b7d8e8f8dabf9200e4894e973e769abf8893f0a3e"),
 }
 
 
@@ -327,6 +328,13 @@ def run_mine(args):
         "decim_ms_parts": {k: round(v, 1) for k, v in zip(("rho", "eigensolver", "host", "guess"),
                                                           st_end["ms_decim_parts"])},
         "decim_sweeps_last": st_end["decim_sweeps_last"],
+        "decim_conv_last": [float("%.3g" % c) for c in st_end["decim_conv_last"] if c > 0],
+        "sigma_shape": {"tile_n": st_end["sigma_tile_n"], "kchunk": st_end["sigma_kchunk"],
+                        "tunes": st_end["tunes"], "tune_hits": st_end["tune_hits"],
+                        "tune_ms": round(st_end["ms_tune"], 1),
+                        "last_candidates_ms": [round(c, 3) for c in st_end["tune_cand_ms"]]},
+        "decim_blocks_last": [st_end["decim_nmat_last"], st_end["decim_nmax_last"]],
+        "decim_sweeps32_last": st_end["decim_sweeps32_last"],
         "sigma_terms": st_end["n_terms"], "sigma_items": st_end["n_items"],
         "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -366,28 +374,43 @@ def run_sigma_probe(args):
     k = K // 2
     td = tempfile.mkdtemp(prefix="dmrg_sigma_")
     h, L, bonds, path = make_inputs(w, td, k)
-    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision])
+    nv = max(1, args.nvec)
+    # nvec > 1: the plan launches nvec vectors per grouped launch (several
+    # Davidson vectors / roots at once); compared with nvec single-vector calls
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision], n_roots=nv)
     plan.set_bond(k)
-    x = torch.from_numpy(si.random_vector(plan.dim, seed=1)).cuda()
+    x = torch.from_numpy(np.concatenate([si.random_vector(plan.dim, seed=1 + v) for v in range(nv)])).cuda()
     y = torch.empty_like(x)
     st = plan.stats()
-    ms = []
-    for i in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("sigma")
-        e0.record()
-        plan.sigma(x, y)
-        e1.record()
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            ms.append(e0.elapsed_time(e1))
-    t = statistics.median(ms)
+
+    def timed(fn):
+        out = []
+        for i in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("sigma")
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    t = timed(lambda: plan.sigma(x, y, nvec=nv))
+    extra = {}
+    if nv > 1:
+        d = plan.dim
+        t1 = timed(lambda: [plan.sigma(x[v * d:(v + 1) * d], y[v * d:(v + 1) * d]) for v in range(nv)])
+        extra = {"nvec": nv, "sigma_ms_one_vector_per_call": round(t1, 3),
+                 "sigma_tflops_one_vector_per_call": round(nv * st["sigma_flops"] / t1 / 1e9, 3)}
     print(json.dumps({"mode": "sigma-only", "workload": args.workload, "precision": args.precision,
-                      "sigma_ms": round(t, 3), "sigma_tflops": round(st["sigma_flops"] / t / 1e9, 3),
+                      "sigma_ms": round(t, 3), "sigma_tflops": round(nv * st["sigma_flops"] / t / 1e9, 3), **extra,
                       "sigma_flops": st["sigma_flops"], "tiles": st["sigma_tiles"], "stages": st["sigma_stages"],
-                      "mma_flops": st["sigma_mma_flops"], "store_bytes": st["store_bytes"]}), flush=True)
+                      "mma_flops": st["sigma_mma_flops"], "store_bytes": st["store_bytes"],
+                      "tile_n": st["sigma_tile_n"], "kchunk": st["sigma_kchunk"],
+                      "tune_candidates_ms": st["tune_cand_ms"], "tune_ms": st["ms_tune"]}), flush=True)
     plan.close()
 
 
@@ -434,6 +457,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nvec", type=int, default=1, help="--sigma-only: vectors per grouped sigma launch")
     ap.add_argument("--sigma-only", action="store_true",
                     help="time sigma calls at the middle bond (NVTX range 'sigma'); for profiling")
     args = ap.parse_args()

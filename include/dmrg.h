@@ -100,6 +100,14 @@ typedef struct {
                                psi and the tensor-core launches) captured once per bond and
                                vector count, with psi / sigma staged through plan buffers;
                                default 1 */
+    int sigma_tune;         /* mixed modes: 1 = the tile shape of the sigma work lists
+                               (tile width 128 or 64, phase-2 K-chunk) is picked per bond by
+                               timing each candidate on a sample of the bond's own work (every
+                               8th output block with all its products); choices are cached by
+                               the bond's sector-size histogram; ignored when tc_kchunk > 0
+                               or sigma_tile_n > 0; default 1 */
+    int sigma_tile_n;       /* mixed modes: 64 or 128 fixes the tile width of the sigma work
+                               lists (no tuning); 0 = tuned or 128; default 0 */
 } dmrg_options;
 
 typedef struct {
@@ -124,12 +132,25 @@ typedef struct {
     int64_t sigma_maps;           /* mixed sigma: tensor maps of the current bond */
     double ms_decim_parts[4];     /* decimation: density matrices, eigensolver, host
                                      selection / new site tensor, next-bond guess (all calls) */
-    int decim_sweeps_last;        /* block-Jacobi sweeps of the last decimation */
+    int decim_sweeps_last;        /* block-Jacobi FP64 sweeps of the last decimation */
     double ms_sigma_dev;          /* device time of all completed sigma calls (CUDA events on
                                      the launching stream around each call) */
     double sigma_flops_dev;       /* algorithmic FLOPs of those calls (all vectors) */
     int64_t sigma_stages_dev;     /* mixed sigma: tensor-core K stages of those calls */
     int64_t sigma_timed;          /* number of sigma calls in ms_sigma_dev */
+    double decim_conv_last[41];   /* last decimation: max over its matrices of off(rho)/|rho|
+                                     before each eigensolver sweep (FP32 stage, then FP64) and
+                                     at the end (0 after the last) */
+    int decim_nmat_last;          /* last decimation: number of density-matrix blocks */
+    int decim_nmax_last;          /* last decimation: largest block dimension */
+    int decim_sweeps32_last;      /* last decimation: FP32 sweeps before the FP64 ones (0: FP64 only) */
+    int sigma_tile_n;             /* mixed sigma: tile width of the current bond's work lists */
+    int64_t sigma_kchunk;         /* mixed sigma: phase-2 K-chunk of the current bond */
+    int64_t tunes;                /* autotuner runs (histograms not seen before) */
+    int64_t tune_hits;            /* bonds whose histogram was already tuned */
+    double ms_tune;               /* wall time of all autotuner runs */
+    double tune_cand_ms[4];       /* last autotuner run: sample time per candidate
+                                     (128 / K-chunk, 64 / K-chunk, 128 / half K-chunk, 64 / half) */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

@@ -25,7 +25,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_roots", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("max_space", C.c_int), ("precond", C.c_int), ("fp64_final", C.c_int),
                 ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
-                ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int)]
+                ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int),
+                ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -39,7 +40,11 @@ class Stats(C.Structure):
                 ("ms_host_plan", C.c_double), ("sigma_tiles", C.c_int64 * 2), ("sigma_stages", C.c_int64 * 2),
                 ("sigma_mma_flops", C.c_double), ("sigma_maps", C.c_int64), ("ms_decim_parts", C.c_double * 4),
                 ("decim_sweeps_last", C.c_int), ("ms_sigma_dev", C.c_double), ("sigma_flops_dev", C.c_double),
-                ("sigma_stages_dev", C.c_int64), ("sigma_timed", C.c_int64)]
+                ("sigma_stages_dev", C.c_int64), ("sigma_timed", C.c_int64), ("decim_conv_last", C.c_double * 41),
+                ("decim_nmat_last", C.c_int), ("decim_nmax_last", C.c_int), ("decim_sweeps32_last", C.c_int),
+                ("sigma_tile_n", C.c_int),
+                ("sigma_kchunk", C.c_int64), ("tunes", C.c_int64), ("tune_hits", C.c_int64), ("ms_tune", C.c_double),
+                ("tune_cand_ms", C.c_double * 4)]
 
     def as_dict(self):
         d = {}

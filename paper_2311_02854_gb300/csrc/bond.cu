@@ -155,6 +155,126 @@ TcBufs sigma_bufs(Plan& P, int k, double* out) {
     return tb;
 }
 
+// ---------------------------------------------------------------------------
+// Tile-shape autotuner of the mixed sigma
+// ---------------------------------------------------------------------------
+
+// Key of the bond's sector-size histogram, coarse enough that the bonds of one
+// region of a sweep share it: the size classes (limits 16 ... 384) of the
+// largest row and column sector, the number of sectors, of psi elements and
+// of terms on a log2 scale, the piece count and the vectors per launch.
+uint64_t sector_histogram_key(const Plan& P, int G) {
+    static const int cuts[7] = {16, 32, 64, 128, 192, 256, 384};
+    auto cls = [&](int d) {
+        int c = 0;
+        while (c < 7 && d > cuts[c]) ++c;
+        return c;
+    };
+    auto lg = [](int64_t x) {
+        int l = 0;
+        while (((int64_t)1 << l) <= x) ++l;
+        return l;
+    };
+    int dl = 0, dr = 0;
+    for (const Plan::Sector& s : P.layout) {
+        dl = std::max(dl, s.dl);
+        dr = std::max(dr, s.dr);
+    }
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t x) {
+        h ^= x;
+        h *= 1099511628211ull;
+    };
+    mix((uint64_t)P.nsplit);
+    mix((uint64_t)G);
+    mix((uint64_t)cls(dl));
+    mix((uint64_t)cls(dr));
+    mix((uint64_t)lg((int64_t)P.layout.size()));
+    mix((uint64_t)lg(P.dim));
+    mix((uint64_t)lg((int64_t)P.sp.terms.size()));
+    return h;
+}
+
+struct SigmaShape {
+    int tn;
+    int64_t kchunk;
+};
+
+// Times the candidate shapes (tile width 128 / 64, phase-2 K-chunk kmax /
+// kmax/2) on a sample of the bond's work list: every 8th output block with all
+// of its products, lowered exactly as the full list would be.  Each candidate
+// runs once to warm up and twice timed (CUDA events on the plan's stream); the
+// fastest wins, the default (128, kmax) unless another is 2 % faster.
+SigmaShape tune_sigma_shape(Plan& P, int k, const ProductList& tl, int64_t cap, int64_t kmax, const int64_t* vs,
+                            int G) {
+    const uint64_t key = sector_histogram_key(P, G);
+    auto f = P.tune_cache.find(key);
+    if (f != P.tune_cache.end()) {
+        ++P.stats.tune_hits;
+        return {f->second.first, f->second.second};
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t khalf = std::max<int64_t>(kmax / 2, 64);
+    const SigmaShape cand[4] = {{128, kmax}, {64, kmax}, {128, khalf}, {64, khalf}};
+    const int stride = tl.outs.size() >= 64 ? 8 : 1;
+    ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
+    // a fixed nonzero bf16 pattern in psi's pieces (the sample is timed, not used)
+    DMRG_CHECK_CUDA(cudaMemsetAsync(P.ps_hi, 0x3c, (size_t)P.n_ppc * 2, P.stream));
+    DMRG_CHECK_CUDA(cudaMemsetAsync(P.ps_lo, 0x3c, (size_t)P.n_ppc * 2 * P.lo_pieces(), P.stream));
+    double* out = P.alloc(std::max<int64_t>(P.dim, 1));
+    cudaEvent_t e0 = P.take_event(), e1 = P.take_event();
+    double best = 0.0;
+    int bi = 0;
+    ProductList smp;
+    try {
+        for (int c = 0; c < 4; ++c) {
+            smp.clear();
+            smp.outs = tl.outs;
+            for (const Contrib& x : tl.cs)
+                if (x.out % stride == 0) smp.cs.push_back(x);
+            smp.lower_tma(BUF_SCR, BUF_ID, P.id_n, cap, cand[c].kchunk, TC_ATOMIC_F64, vs, G, cand[c].tn);
+            smp.cs.clear();
+            ensure_scratch(P, (int64_t)G * smp.scratch_elems);
+            for (auto& ch : smp.tchunks) {
+                ch.first.upload(P.stream);
+                ch.second.upload(P.stream);
+            }
+            const TcBufs tb = sigma_bufs(P, k, out);
+            smp.maps.encode_upload(tb, P.nsplit, P.stream);
+            tc_prepare(P.nsplit);
+            float ms = 0.f, msb = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                DMRG_CHECK_CUDA(cudaEventRecord(e0, P.stream));
+                smp.run_tma(tb, 1, P.nsplit, P.stream);
+                DMRG_CHECK_CUDA(cudaEventRecord(e1, P.stream));
+                DMRG_CHECK_CUDA(cudaEventSynchronize(e1));
+                DMRG_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep == 1 || (rep > 1 && ms < msb)) msb = ms;
+            }
+            P.check_device_error();
+            P.stats.tune_cand_ms[c] = msb;
+            if (c == 0 || msb < 0.98 * best) {
+                best = msb;
+                bi = c;
+            }
+        }
+    } catch (...) {
+        smp.clear();
+        P.free(out, std::max<int64_t>(P.dim, 1));
+        P.ev_pool.push_back(e0);
+        P.ev_pool.push_back(e1);
+        throw;
+    }
+    smp.clear();
+    P.free(out, std::max<int64_t>(P.dim, 1));
+    P.ev_pool.push_back(e0);
+    P.ev_pool.push_back(e1);
+    P.tune_cache[key] = {cand[bi].tn, cand[bi].kchunk};
+    ++P.stats.tunes;
+    P.stats.ms_tune += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return cand[bi];
+}
+
 }  // namespace
 
 void free_block(Plan& P, std::unique_ptr<Block>& b) {
@@ -528,6 +648,9 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     ensure_ident(P, maxd);
     const int64_t cap = scratch_cap(P);
     if (P.tc_store()) {
+        // the cp.async-staged engine: renormalisation lists hold many short
+        // products (K-chunks of 256), where it measured faster than the
+        // TMA-staged engine of sigma (map encoding and lowering cost included)
         pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F64);
         P.stats.ms_host_plan += host_ms_since(host0);
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 8));
@@ -729,9 +852,13 @@ void set_bond(Plan& P, int k) {
         const int G = std::max(1, P.opt.n_roots);
         int64_t vs[kMaxBufs] = {};
         vs[BUF_PSI] = P.dim_pad;
-        tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, std::max<int64_t>(scratch_cap(P) / G, 1 << 20),
-                     P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC),
-                     TC_ATOMIC_F64, vs, G);
+        const int64_t cap = std::max<int64_t>(scratch_cap(P) / G, 1 << 20);
+        SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
+        if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
+        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0) shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
+        tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, cap, shape.kchunk, TC_ATOMIC_F64, vs, G, shape.tn);
+        P.stats.sigma_tile_n = shape.tn;
+        P.stats.sigma_kchunk = shape.kchunk;
         tl.cs.clear();
         for (int ph = 0; ph < 2; ++ph) P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
         P.stats.sigma_mma_flops = 0.0;

@@ -153,6 +153,8 @@ void dmrg_default_options(dmrg_options* o) {
     o->tc_kchunk = 0;
     o->fp64_store = 0;
     o->sigma_graph = 1;
+    o->sigma_tune = 1;
+    o->sigma_tile_n = 0;
 }
 
 const char* dmrg_version(void) {
@@ -182,6 +184,8 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         else if (P.opt.precision == DMRG_BF16) P.nsplit = 1;
         else if (P.opt.precision == DMRG_BF16X6) P.nsplit = 3;
         else throw Error(DMRG_EINVAL, "unknown precision mode");
+        if (P.opt.sigma_tile_n != 0 && P.opt.sigma_tile_n != 64 && P.opt.sigma_tile_n != 128)
+            throw Error(DMRG_EINVAL, "sigma_tile_n must be 0, 64 or 128");
         P.K = K;
         P.N = N;
         P.twoS = twoS;

@@ -32,7 +32,9 @@ struct Tile {
     uint8_t c_buf, mode;
     uint16_t nst;         // tensor-core engine: 64-deep K stages of the tile (set by the TMA work list)
     float alpha;          // epilogue scale (tensor-core engine; the FP64 engine scales per segment)
+    int32_t tn;           // TMA tensor-core engine: tile width (64 or 128 columns)
 };
+static_assert(sizeof(Tile) == 48, "Tile keeps its 48-byte record");
 
 constexpr int kMaxBufs = 8;
 // Base pointers of the buffers a work list refers to, with the per-vector

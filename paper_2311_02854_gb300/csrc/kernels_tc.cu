@@ -221,7 +221,7 @@ __device__ __forceinline__ void epilogue_tile(const Tile& T, int v, int nst, uin
     __syncwarp();
     if (lane == 0) mbar_arrive(tempty);
     if (!rok || (nst == 0 && (T.mode == TC_ATOMIC_F64 || T.mode == TC_ATOMIC_F32))) return;
-    const int ncol = min(TN, T.n - T.n0);
+    const int ncol = min(T.tn > 0 ? T.tn : TN, T.n - T.n0);  // the FP64-engine work list leaves tn 0
     const int64_t off = T.c_off + (int64_t)r * T.ldc + T.n0 + (int64_t)v * B.out_vstride[T.c_buf];
     if (T.mode == TC_ATOMIC_F64) {
         double* o = (double*)B.out[T.c_buf] + off;
@@ -548,8 +548,9 @@ __global__ void __launch_bounds__(THREADS3, 1)
                 const Tile T = tiles[t % ntiles];
                 const int nst = T.nst;
                 // a second 64-row (or 64-column) half only when the block extends past the first
-                const int nA = (T.m - T.m0 > 64) ? 2 : 1, nB = (T.n - T.n0 > 64) ? 2 : 1;
-                const int n16 = (min(TN, T.n - T.n0) + 15) / 16;
+                const int ncol = min(T.tn, T.n - T.n0);  // columns of this tile
+                const int nA = (T.m - T.m0 > 64) ? 2 : 1, nB = (ncol > 64) ? 2 : 1;
+                const int n16 = (ncol + 15) / 16;
                 if (nst == 0) {
                     if (q >= (uint32_t)S && !mbar_wait(smem_u32(&empty_bar[q % S]), ((q / S) - 1) & 1u)) {
                         failed = true;
@@ -783,8 +784,9 @@ void launch_seg_gemm_tc(const WorkList& w, const TcBufs& b, int nvec, int nsplit
 // ---------------------------------------------------------------------------
 
 void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<TSeg>& s, uint8_t mode,
-                            int64_t kchunk, float alpha) {
+                            int64_t kchunk, float alpha, int tn) {
     if (m <= 0 || n <= 0) return;
+    DMRG_REQUIRE(tn == 64 || tn == TN, DMRG_EINVAL, "tile width must be 64 or 128");
     std::vector<std::pair<int, int>> chunks;
     const bool atomic = (mode == TC_ATOMIC_F64 || mode == TC_ATOMIC_F32);
     if (atomic && kchunk > 0) {
@@ -812,8 +814,9 @@ void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, con
         DMRG_REQUIRE(nst < 65536, DMRG_EINVAL, "tile with too many K stages (use a K-chunk)");
         const int se = (int)segs.size();
         for (int m0 = 0; m0 < m; m0 += TM)
-            for (int n0 = 0; n0 < n; n0 += TN) {
+            for (int n0 = 0; n0 < n; n0 += tn) {
                 Tile t{};
+                t.tn = tn;
                 t.alpha = alpha;
                 t.c_off = c_off;
                 t.ldc = ldc;

@@ -546,7 +546,7 @@ TSeg make_tseg(MapTable& mt, const View& A, const View& B, int m, int n, int k, 
 }  // namespace
 
 void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t kchunk, uint8_t out_mode,
-                            const int64_t* vstride_in, int nv) {
+                            const int64_t* vstride_in, int nv, int tile_n) {
     const int8_t sbuf = sbuf_;
     this->sbuf = sbuf_;
     release();
@@ -669,18 +669,18 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
                 if (it.pq_first) {
                     flops += 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
                     p1.add_block(T.off, sbuf, c.m, c.k2, T.ld, {make_tseg(maps, c.P, c.Q, c.m, c.k2, c.k1, 1.0, vstride, nv)},
-                                 TC_STORE_SPLIT, 0, (float)c.alpha);
+                                 TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
                     sv.push_back(make_tseg(maps, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv));
                 } else {
                     flops += 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
                     p1.add_block(T.off, sbuf, c.k1, c.n, T.ld, {make_tseg(maps, c.Q, c.R, c.k1, c.n, c.k2, 1.0, vstride, nv)},
-                                 TC_STORE_SPLIT, 0, (float)c.alpha);
+                                 TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
                     sv.push_back(make_tseg(maps, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv));
                 }
             } else if (it.kind == 2) {
                 flops += it.fl;
                 p1.add_block(T.off, sbuf, c.m, c.n, T.ld, {make_tseg(maps, it.X, it.Y, c.m, c.n, it.k, 1.0, vstride, nv)},
-                             TC_STORE_SPLIT, 0, (float)c.alpha);
+                             TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
                 sv.push_back(make_tseg(maps, T, I, c.m, c.n, c.n, 1.0, vstride, nv));
             } else {
                 flops += it.fl;
@@ -689,7 +689,7 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         }
         for (int o : order) {
             const OutBlock& ob = outs[o];
-            p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 1.0f);
+            p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 1.0f, tile_n);
         }
         scratch_elems = std::max(scratch_elems, used);
         tchunks.emplace_back(std::move(p1), std::move(p2));

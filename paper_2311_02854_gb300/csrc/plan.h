@@ -83,7 +83,7 @@ struct ProductList {
     // tensor.  vec_bufs: buffers holding one copy per vector (stride vstride[b],
     // nv copies); the maps are encoded later by maps.encode_upload.
     void lower_tma(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk,
-                   uint8_t out_mode, const int64_t* vstride, int nv);
+                   uint8_t out_mode, const int64_t* vstride, int nv, int tile_n = 128);
     void run_tma(const TcBufs& tb, int nvec, int nsplit, cudaStream_t st);
     std::vector<std::pair<TmaWorkList, TmaWorkList>> tchunks;
     MapTable maps;
@@ -185,6 +185,8 @@ struct Plan {
         int64_t stages;
     };
     std::vector<SigmaEvents> sig_pending;
+    // tile-shape autotuner: sector-size histogram key -> (tile width, phase-2 K-chunk)
+    std::map<uint64_t, std::pair<int, int64_t>> tune_cache;
     std::vector<cudaEvent_t> ev_pool;
     cudaEvent_t take_event();
     void collect_sigma_times(bool wait);

@@ -444,8 +444,14 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         jobs.push_back(j);
         DMRG_REQUIRE(g.n <= 16384, DMRG_EINVAL, "density-matrix sector larger than 16384");
     }
+    std::vector<double> conv;
     P.stats.decim_sweeps_last = block_jacobi_eigh(
-        jobs, 40, 1e-14, st, [&](int64_t n) { return P.alloc(n); }, [&](double* p, int64_t n) { P.free(p, n); });
+        jobs, 40, 1e-14, st, [&](int64_t n) { return P.alloc(n); }, [&](double* p, int64_t n) { P.free(p, n); },
+        &conv, &P.stats.decim_sweeps32_last);
+    for (int i = 0; i < 41; ++i) P.stats.decim_conv_last[i] = i < (int)conv.size() ? conv[i] : 0.0;
+    P.stats.decim_nmat_last = (int)jobs.size();
+    P.stats.decim_nmax_last = 0;
+    for (auto& j : jobs) P.stats.decim_nmax_last = std::max(P.stats.decim_nmax_last, (int)j.n);
     const auto hd2 = std::chrono::steady_clock::now();
     std::vector<double> hw(woff), hv(rho_tot);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hw.data(), d_w, woff * 8, cudaMemcpyDeviceToHost, st));

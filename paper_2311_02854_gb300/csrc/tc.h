@@ -68,10 +68,10 @@ struct TmaWorkList {
     Tile* d_tiles = nullptr;
     TSeg* d_segs = nullptr;
     size_t cap_tiles = 0, cap_segs = 0;
-    // output block (m x n, ld ldc) at c_off of c_buf, 128 x 128 tiles, split into
-    // K-chunks of at most kchunk (atomic modes only)
+    // output block (m x n, ld ldc) at c_off of c_buf, 128 x tn tiles (tn = 64 or
+    // 128), split into K-chunks of at most kchunk (atomic modes only)
     void add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<TSeg>& s, uint8_t mode,
-                   int64_t kchunk, float alpha);
+                   int64_t kchunk, float alpha, int tn = 128);
     void upload(cudaStream_t st);
     void release();
 };
