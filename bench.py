@@ -115,8 +115,8 @@ class ClockSampler:
 # call.  The traffic of a sigma call in the timed steps is taken in proportion to
 # its stages; it is reported only while the kernel source is the one captured.
 SIGMA_TRAFFIC = {
-    "k73_d3000:bf16x3": dict(bytes=1405.693e9 + 249.750e9, stages=33096283 + 31440895,
-                             kernel_sha256="b9a1c588ded3f8bdc26f7b9b7d8e8f8dabf9200e4894e973e769abf8893f0a3e"),
+    "k73_d3000:bf16x3": dict(bytes=1416.604e9 + 245.834e9, stages=33096283 + 31440895,
+                             kernel_sha256="7e607aea19e15606cd3ad47b6db602e73418b24d046e9deef4d20ade31b169cd"),
 }
 
 

@@ -103,7 +103,8 @@ typedef struct {
     int sigma_tune;         /* mixed modes: 1 = the tile shape of the sigma work lists
                                (tile width 128 or 64, phase-2 K-chunk) is picked per bond by
                                timing each candidate on a sample of the bond's own work (every
-                               8th output block with all its products); choices are cached by
+                               8th output block, 16th beyond a million products, with all their
+                               products); choices are cached by
                                the bond's sector-size histogram; ignored when tc_kchunk > 0
                                or sigma_tile_n > 0; default 1 */
     int sigma_tile_n;       /* mixed modes: 64 or 128 fixes the tile width of the sigma work

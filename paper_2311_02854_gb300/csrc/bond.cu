@@ -201,10 +201,11 @@ struct SigmaShape {
 };
 
 // Times the candidate shapes (tile width 128 / 64, phase-2 K-chunk kmax /
-// kmax/2) on a sample of the bond's work list: every 8th output block with all
-// of its products, lowered exactly as the full list would be.  Each candidate
-// runs once to warm up and twice timed (CUDA events on the plan's stream); the
-// fastest wins, the default (128, kmax) unless another is 2 % faster.
+// kmax/2) on a sample of the bond's work list: every 8th (16th) output block
+// with all of its products, lowered exactly as the full list would be.  Each
+// candidate runs once to warm up and once timed (CUDA events on the plan's
+// stream); the fastest wins, the default (128, kmax) unless another is 2 %
+// faster.
 SigmaShape tune_sigma_shape(Plan& P, int k, const ProductList& tl, int64_t cap, int64_t kmax, const int64_t* vs,
                             int G) {
     const uint64_t key = sector_histogram_key(P, G);
@@ -216,7 +217,8 @@ SigmaShape tune_sigma_shape(Plan& P, int k, const ProductList& tl, int64_t cap, 
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t khalf = std::max<int64_t>(kmax / 2, 64);
     const SigmaShape cand[4] = {{128, kmax}, {64, kmax}, {128, khalf}, {64, khalf}};
-    const int stride = tl.outs.size() >= 64 ? 8 : 1;
+    // every 8th output (16th for lists of over a million products)
+    const int stride = tl.outs.size() >= 64 ? (tl.cs.size() > ((size_t)1 << 20) ? 16 : 8) : 1;
     ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
     // a fixed nonzero bf16 pattern in psi's pieces (the sample is timed, not used)
     DMRG_CHECK_CUDA(cudaMemsetAsync(P.ps_hi, 0x3c, (size_t)P.n_ppc * 2, P.stream));
@@ -242,14 +244,13 @@ SigmaShape tune_sigma_shape(Plan& P, int k, const ProductList& tl, int64_t cap, 
             const TcBufs tb = sigma_bufs(P, k, out);
             smp.maps.encode_upload(tb, P.nsplit, P.stream);
             tc_prepare(P.nsplit);
-            float ms = 0.f, msb = 0.f;
-            for (int rep = 0; rep < 3; ++rep) {
+            float msb = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {  // a warm-up run, then the timed one
                 DMRG_CHECK_CUDA(cudaEventRecord(e0, P.stream));
                 smp.run_tma(tb, 1, P.nsplit, P.stream);
                 DMRG_CHECK_CUDA(cudaEventRecord(e1, P.stream));
                 DMRG_CHECK_CUDA(cudaEventSynchronize(e1));
-                DMRG_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep == 1 || (rep > 1 && ms < msb)) msb = ms;
+                DMRG_CHECK_CUDA(cudaEventElapsedTime(&msb, e0, e1));
             }
             P.check_device_error();
             P.stats.tune_cand_ms[c] = msb;
@@ -537,6 +538,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     out->n = std::max<int64_t>(OL.total, 32);
 
     const auto host0 = std::chrono::steady_clock::now();
+    double host_lower_ms = 0.0;
     ProductList pl;
     std::vector<std::array<int, 3>> keys;
     for (auto& kv : P.mps.sites[m]) keys.push_back(kv.first);
@@ -652,7 +654,8 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
         // products (K-chunks of 256), where it measured faster than the
         // TMA-staged engine of sigma (map encoding and lowering cost included)
         pl.lower_tc(BUF_SCR, BUF_ID, P.id_n, cap, kChunkTC, TC_ATOMIC_F64);
-        P.stats.ms_host_plan += host_ms_since(host0);
+        host_lower_ms = host_ms_since(host0);
+        P.stats.ms_host_plan += host_lower_ms;
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 8));
         pl.upload(P.stream);
         double* acc = P.alloc(out->n);
@@ -674,7 +677,8 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
         P.free(acc, out->n);
     } else {
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, kChunkF64);
-        P.stats.ms_host_plan += host_ms_since(host0);
+        host_lower_ms = host_ms_since(host0);
+        P.stats.ms_host_plan += host_lower_ms;
         ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1));
         pl.upload(P.stream);
         out->d = P.alloc(out->n);
@@ -699,6 +703,10 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     cudaEventElapsedTime(&ms, e0, e1);
     P.stats.ms_renorm += ms;
     P.stats.renorm_flops_last = pl.flops + fl_int;
+    if (P.opt.verbose)
+        fprintf(stderr, "[dmrg] renormalise site %d (%s): %.0f ms, of which host lowering %.0f ms; %zu products, "
+                        "%.3g FLOP\n",
+                m, forward ? "forward" : "backward", ms, host_lower_ms, pl.cs.size(), pl.flops + fl_int);
     pl.release();
     free_interms(P, IS);
     free_site(P, A);
@@ -791,50 +799,63 @@ void set_bond(Plan& P, int k) {
     pl.clear();
     for (const Plan::Sector& s : P.layout) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
     const LocalOps& Y = P.sp.y;
-    int64_t nitems = 0;
-    // the blocks of a term's operators depend only on the ket sector of their side
+    // the blocks of a term's operators depend only on the ket sector of their
+    // side; terms are taken in blocks on host threads and their contributions
+    // concatenated in term order
     const int nbl = L.lay.basis.size(), nbr = R.lay.basis.size();
-    std::vector<OpLookup> lcache(nbl), rcache(nbr);
-    for (const Term3& t : P.sp.terms) {
-        const LocalOp& M = Y.ops[t.y];
-        const int pR = ref_parity(R.lay, P.sp.interms, t.R);
-        for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
-        for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
-        for (size_t si = 0; si < P.layout.size(); ++si) {
-            const Plan::Sector& s = P.layout[si];
-            const OpLookup& ol = lcache[s.il];
-            if (!ol.ok) continue;
-            const OpLookup& orr = rcache[s.ir];
-            if (!orr.ok) continue;
-            const int nl = L.lay.basis.qn[s.il].n;
-            const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
-            for (int y2 = 0; y2 < 16; ++y2) {
-                const double mv = M.at(y2, s.y);
-                if (mv == 0.0) continue;
-                const int os = P.sector_idx[16 * ol.j + y2];
-                if (os < 0) continue;
-                const Plan::Sector& o = P.layout[os];
-                DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
-                const int e = M.parity * nl + pR * (nl + ny);
-                const double zeta = (e & 1) ? -1.0 : 1.0;
-                Contrib c;
-                c.out = os;
-                c.P = ol.v;  // O^L_eff : d_jl x d_il
-                c.Q.buf = BUF_PSI;
-                c.Q.off = s.off;
-                c.Q.ld = s.dr;  // Psi_s : d_il x d_ir
-                c.R = orr.v.T();  // (O^R_eff)^T : d_ir x d_jr
-                c.m = o.dl;
-                c.k1 = s.dl;
-                c.k2 = s.dr;
-                c.n = o.dr;
-                c.alpha = t.c * zeta * mv;
-                c.qsec = (int)si;
-                pl.cs.push_back(c);
-                ++nitems;
+    const size_t nterm = P.sp.terms.size();
+    const size_t tblk = std::max<size_t>(1, (nterm + 63) / 64);
+    const size_t nblk = (nterm + tblk - 1) / tblk;
+    std::vector<std::vector<Contrib>> part(nblk);
+    parallel_for(nblk, [&](size_t b) {
+        std::vector<OpLookup> lcache(nbl), rcache(nbr);
+        std::vector<Contrib>& out = part[b];
+        for (size_t ti = b * tblk; ti < std::min(nterm, (b + 1) * tblk); ++ti) {
+            const Term3& t = P.sp.terms[ti];
+            const LocalOp& M = Y.ops[t.y];
+            const int pR = ref_parity(R.lay, P.sp.interms, t.R);
+            for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
+            for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
+            for (size_t si = 0; si < P.layout.size(); ++si) {
+                const Plan::Sector& s = P.layout[si];
+                const OpLookup& ol = lcache[s.il];
+                if (!ol.ok) continue;
+                const OpLookup& orr = rcache[s.ir];
+                if (!orr.ok) continue;
+                const int nl = L.lay.basis.qn[s.il].n;
+                const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
+                for (int y2 = 0; y2 < 16; ++y2) {
+                    const double mv = M.at(y2, s.y);
+                    if (mv == 0.0) continue;
+                    const int os = P.sector_idx[16 * ol.j + y2];
+                    if (os < 0) continue;
+                    const Plan::Sector& o = P.layout[os];
+                    DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
+                    const int e = M.parity * nl + pR * (nl + ny);
+                    const double zeta = (e & 1) ? -1.0 : 1.0;
+                    Contrib c;
+                    c.out = os;
+                    c.P = ol.v;  // O^L_eff : d_jl x d_il
+                    c.Q.buf = BUF_PSI;
+                    c.Q.off = s.off;
+                    c.Q.ld = s.dr;  // Psi_s : d_il x d_ir
+                    c.R = orr.v.T();  // (O^R_eff)^T : d_ir x d_jr
+                    c.m = o.dl;
+                    c.k1 = s.dl;
+                    c.k2 = s.dr;
+                    c.n = o.dr;
+                    c.alpha = t.c * zeta * mv;
+                    c.qsec = (int)si;
+                    out.push_back(c);
+                }
             }
         }
-    }
+    });
+    size_t ntot = 0;
+    for (auto& v : part) ntot += v.size();
+    pl.cs.reserve(ntot);
+    for (auto& v : part) pl.cs.insert(pl.cs.end(), v.begin(), v.end());
+    const int64_t nitems = (int64_t)ntot;
     int maxd = std::max({L.lay.basis.dmax(), R.lay.basis.dmax(), 1});
     ensure_ident(P, maxd);
     P.sigma_fp64_ready = false;
@@ -854,9 +875,12 @@ void set_bond(Plan& P, int k) {
         vs[BUF_PSI] = P.dim_pad;
         const int64_t cap = std::max<int64_t>(scratch_cap(P) / G, 1 << 20);
         SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
+        const double t_terms = host_ms_since(hs0);
         if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
         else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0) shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
+        const double t_tune = host_ms_since(hs0);
         tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, cap, shape.kchunk, TC_ATOMIC_F64, vs, G, shape.tn);
+        const double t_lower = host_ms_since(hs0);
         P.stats.sigma_tile_n = shape.tn;
         P.stats.sigma_kchunk = shape.kchunk;
         tl.cs.clear();
@@ -880,6 +904,10 @@ void set_bond(Plan& P, int k) {
             ch.second.upload(P.stream);
         }
         tl.maps.encode_upload(sigma_bufs(P, k, nullptr), P.nsplit, P.stream);
+        if (P.opt.verbose)
+            fprintf(stderr, "[dmrg] bond %d sigma planning: terms %.0f ms, tuning %.0f ms, lowering %.0f ms, "
+                            "upload %.0f ms (%zu chunks)\n",
+                    k, t_terms, t_tune - t_terms, t_lower - t_tune, host_ms_since(hs0) - t_lower, tl.tchunks.size());
         P.stats.sigma_maps = (int64_t)tl.maps.keys.size();
         P.stats.sigma_flops = tl.flops;
         // padded bf16 copy of psi: one split job per sector
@@ -908,6 +936,7 @@ void set_bond(Plan& P, int k) {
     {
         WorkList w;
         std::vector<std::vector<Seg>> per(P.layout.size());
+        std::vector<OpLookup> lcache(nbl), rcache(nbr);
         for (const Term3& t : P.sp.terms) {
             const LocalOp& M = Y.ops[t.y];
             if (M.dq != QN(0, 0)) continue;

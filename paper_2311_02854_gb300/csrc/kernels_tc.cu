@@ -834,10 +834,24 @@ void TmaWorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, con
     }
 }
 
-void TmaWorkList::upload(cudaStream_t st) {
+void TmaWorkList::order_tiles() {
     // longest tiles first: CTAs take tiles round-robin, so the short ones fill
-    // in at the end of the launch instead of a few long ones trailing
-    std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& a, const Tile& b) { return a.nst > b.nst; });
+    // in at the end of the launch instead of a few long ones trailing.  A
+    // stable counting sort on the stage count (< 65536): two linear passes
+    // instead of an n log n sort of millions of records on every bond
+    if (tiles.size() > 1) {
+        int maxn = 0;
+        for (const Tile& t : tiles) maxn = std::max(maxn, (int)t.nst);
+        std::vector<size_t> pos((size_t)maxn + 2, 0);
+        for (const Tile& t : tiles) ++pos[(size_t)(maxn - t.nst) + 1];
+        for (size_t i = 1; i < pos.size(); ++i) pos[i] += pos[i - 1];
+        std::vector<Tile> sorted(tiles.size());
+        for (const Tile& t : tiles) sorted[pos[(size_t)(maxn - t.nst)]++] = t;
+        tiles.swap(sorted);
+    }
+}
+
+void TmaWorkList::upload(cudaStream_t st) {
     if (tiles.size() > cap_tiles) {
         if (d_tiles) cudaFree(d_tiles);
         cap_tiles = tiles.size() + 16;

@@ -2,6 +2,9 @@
 // products onto the segmented GEMM, environments (renormalisation, Eq.
 // Renorm), the bond's intermediates and sigma (Eq. Sigma), diag(H_eff).
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <thread>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -405,35 +408,61 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
     I.buf = ibuf;
     I.off = 0;
     I.ld = ild;
-    size_t i = 0;
-    while (i < cs.size()) {
-        WorkList p1, p2;
+    // scratch elements of a contribution's phase-1 product
+    auto need_of = [&](const Contrib& c) -> int64_t {
+        const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
+        const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
+        if (nreal == 3) {
+            const double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+            const double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+            return cost_pq <= cost_qr ? (int64_t)c.m * round_up(c.k2, 8) : (int64_t)c.k1 * round_up(c.n, 8);
+        }
+        return unit ? 0 : (int64_t)c.m * round_up(c.n, 8);
+    };
+    // chunk boundaries: each chunk's phase-1 products fit the scratch
+    std::vector<size_t> starts{0};
+    {
+        int64_t used = 0;
+        for (size_t i = 0; i < cs.size(); ++i) {
+            const int64_t need = need_of(cs[i]);
+            if (used + need > cap && used > 0) {
+                starts.push_back(i);
+                used = 0;
+            }
+            used += need;
+        }
+    }
+    starts.push_back(cs.size());
+    const size_t nch = cs.empty() ? 0 : starts.size() - 1;
+    std::vector<std::pair<WorkList, WorkList>> built(nch);
+    std::vector<double> cfl(nch, 0.0);
+    std::vector<int64_t> cused(nch, 0);
+    // the chunks' work lists, built in parallel
+    parallel_for(nch, [&](size_t ch) {
+        WorkList& p1 = built[ch].first;
+        WorkList& p2 = built[ch].second;
         std::vector<std::vector<Seg>> segs(outs.size());
         std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;
         int64_t used = 0;
-        for (; i < cs.size(); ++i) {
+        double fl = 0.0;
+        for (size_t i = starts[ch]; i < starts[ch + 1]; ++i) {
             const Contrib& c = cs[i];
             const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
             const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
-            // scratch needed by this contribution
-            int64_t need = 0;
+            const int64_t need = need_of(c);
             bool pq_first = true;
             double cost = 0.0;
-            int tr = 0, tc_ = 0;  // rows / cols of the phase-1 product
+            int tc_ = 0;  // columns of the phase-1 product
             if (nreal == 3) {
-                double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
-                double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                const double cost_pq = 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                const double cost_qr = 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
                 pq_first = cost_pq <= cost_qr;
                 cost = std::min(cost_pq, cost_qr);
-                tr = pq_first ? c.m : c.k1;
                 tc_ = pq_first ? c.k2 : c.n;
             } else if (!unit) {
-                tr = c.m;
                 tc_ = c.n;
             }
-            if (tr > 0) need = (int64_t)tr * round_up(tc_, 8);
-            if (used + need > cap && used > 0) break;
             if (!seen[c.out]) {
                 seen[c.out] = 1;
                 order.push_back(c.out);
@@ -444,7 +473,7 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
             T.off = used;
             T.ld = (int)round_up(std::max(tc_, 1), 8);
             if (nreal == 3) {
-                flops += cost;
+                fl += cost;
                 if (pq_first) {
                     p1.add_block(used, sbuf, c.m, c.k2, T.ld, {make_seg(c.P, c.Q, c.k1, 1.0)}, TC_STORE_SPLIT, 0, 128,
                                  (float)c.alpha);
@@ -474,12 +503,12 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
                     Y = c.R;
                     k = c.k1;
                 }
-                flops += 2.0 * c.m * c.n * k;
+                fl += 2.0 * c.m * c.n * k;
             } else {
                 X = !c.P.ident ? c.P : (!c.Q.ident ? c.Q : c.R);
                 Y = I;
                 k = c.n;
-                flops += 2.0 * c.m * c.n;
+                fl += 2.0 * c.m * c.n;
             }
             if (unit) {
                 sv.push_back(make_seg(X, Y, k, c.alpha));
@@ -494,8 +523,13 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
             const OutBlock& ob = outs[o];
             p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 128, 1.0f);
         }
-        scratch_elems = std::max(scratch_elems, used);
-        chunks.emplace_back(std::move(p1), std::move(p2));
+        cfl[ch] = fl;
+        cused[ch] = used;
+    });
+    for (size_t ch = 0; ch < nch; ++ch) {
+        flops += cfl[ch];
+        scratch_elems = std::max(scratch_elems, cused[ch]);
+        chunks.emplace_back(std::move(built[ch]));
     }
 }
 
@@ -573,13 +607,20 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         int k = 0;
         double fl = 0.0;  // algorithmic FLOPs of a kind 1 / 2 item
     };
-    size_t i = 0;
-    while (i < cs.size()) {
-        // pass 1: the items of this chunk, their phase-1 shapes and scratch groups
+    // pass 1 (sequential): the chunks of the list (each fits the scratch), the
+    // items of each, their phase-1 shapes and scratch groups
+    struct ChunkPlan {
+        size_t i = 0, j = 0;
         std::vector<Item> items;
-        std::unordered_map<int64_t, int> gidx;  // (rows << 32 | cols) -> scratch group
         std::vector<std::array<int64_t, 4>> groups;  // rows, cols, count, base
         int64_t used = 0;
+    };
+    std::vector<ChunkPlan> plans;
+    size_t i = 0;
+    while (i < cs.size()) {
+        ChunkPlan cp;
+        cp.i = i;
+        std::unordered_map<int64_t, int> gidx;  // (rows << 32 | cols) -> scratch group
         size_t j = i;
         for (; j < cs.size(); ++j) {
             const Contrib& c = cs[j];
@@ -623,33 +664,47 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
             }
             int64_t need = 0;
             if (it.kind >= 2) need = (int64_t)it.tr * round_up(it.tcl, 8);
-            if (used + need > cap && used > 0) break;
+            if (cp.used + need > cap && cp.used > 0) break;
             if (it.kind >= 2) {
                 const int64_t key = ((int64_t)it.tr << 32) | (int64_t)it.tcl;
                 auto g = gidx.find(key);
                 if (g == gidx.end()) {
-                    g = gidx.emplace(key, (int)groups.size()).first;
-                    groups.push_back({(int64_t)it.tr, (int64_t)it.tcl, 0, 0});
+                    g = gidx.emplace(key, (int)cp.groups.size()).first;
+                    cp.groups.push_back({(int64_t)it.tr, (int64_t)it.tcl, 0, 0});
                 }
                 it.grp = g->second;
-                it.z = (int)groups[it.grp][2]++;
+                it.z = (int)cp.groups[it.grp][2]++;
             }
-            used += need;
-            items.push_back(it);
+            cp.used += need;
+            cp.items.push_back(it);
         }
         int64_t base = 0;
-        for (auto& g : groups) {
+        for (auto& g : cp.groups) {
             g[3] = base;
             base += g[2] * g[0] * round_up(g[1], 8);
         }
-        // pass 2: work lists
-        TmaWorkList p1, p2;
+        cp.j = j;
+        plans.push_back(std::move(cp));
+        i = j;
+    }
+    // pass 2 (chunks in parallel): the work lists of each chunk, with tensor
+    // maps keyed in a table of the chunk's own, merged into `maps` afterwards
+    const size_t nch = plans.size();
+    std::vector<TmaWorkList> w1(nch), w2(nch);
+    std::vector<MapTable> local(nch);
+    std::vector<double> cfl(nch, 0.0);
+    auto build_chunk = [&](size_t ch) {
+        const ChunkPlan& cp = plans[ch];
+        MapTable& lm = local[ch];
+        TmaWorkList& p1 = w1[ch];
+        TmaWorkList& p2 = w2[ch];
+        double fl = 0.0;
         std::vector<std::vector<TSeg>> segs(outs.size());
         std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;
-        for (size_t q = 0; q < items.size(); ++q) {
-            const Contrib& c = cs[i + q];
-            const Item& it = items[q];
+        for (size_t q = 0; q < cp.items.size(); ++q) {
+            const Contrib& c = cs[cp.i + q];
+            const Item& it = cp.items[q];
             if (!seen[c.out]) {
                 seen[c.out] = 1;
                 order.push_back(c.out);
@@ -657,7 +712,7 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
             std::vector<TSeg>& sv = segs[c.out];
             View T;
             if (it.kind >= 2) {
-                const auto& g = groups[it.grp];
+                const auto& g = cp.groups[it.grp];
                 T.buf = sbuf;
                 T.ld = (int)round_up(g[1], 8);
                 T.zstride = g[0] * T.ld;
@@ -667,33 +722,47 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
             }
             if (it.kind == 3) {
                 if (it.pq_first) {
-                    flops += 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
-                    p1.add_block(T.off, sbuf, c.m, c.k2, T.ld, {make_tseg(maps, c.P, c.Q, c.m, c.k2, c.k1, 1.0, vstride, nv)},
+                    fl += 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
+                    p1.add_block(T.off, sbuf, c.m, c.k2, T.ld, {make_tseg(lm, c.P, c.Q, c.m, c.k2, c.k1, 1.0, vstride, nv)},
                                  TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                    sv.push_back(make_tseg(maps, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv));
+                    sv.push_back(make_tseg(lm, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv));
                 } else {
-                    flops += 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
-                    p1.add_block(T.off, sbuf, c.k1, c.n, T.ld, {make_tseg(maps, c.Q, c.R, c.k1, c.n, c.k2, 1.0, vstride, nv)},
+                    fl += 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
+                    p1.add_block(T.off, sbuf, c.k1, c.n, T.ld, {make_tseg(lm, c.Q, c.R, c.k1, c.n, c.k2, 1.0, vstride, nv)},
                                  TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                    sv.push_back(make_tseg(maps, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv));
+                    sv.push_back(make_tseg(lm, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv));
                 }
             } else if (it.kind == 2) {
-                flops += it.fl;
-                p1.add_block(T.off, sbuf, c.m, c.n, T.ld, {make_tseg(maps, it.X, it.Y, c.m, c.n, it.k, 1.0, vstride, nv)},
+                fl += it.fl;
+                p1.add_block(T.off, sbuf, c.m, c.n, T.ld, {make_tseg(lm, it.X, it.Y, c.m, c.n, it.k, 1.0, vstride, nv)},
                              TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                sv.push_back(make_tseg(maps, T, I, c.m, c.n, c.n, 1.0, vstride, nv));
+                sv.push_back(make_tseg(lm, T, I, c.m, c.n, c.n, 1.0, vstride, nv));
             } else {
-                flops += it.fl;
-                sv.push_back(make_tseg(maps, it.X, it.Y, c.m, c.n, it.k, c.alpha, vstride, nv));
+                fl += it.fl;
+                sv.push_back(make_tseg(lm, it.X, it.Y, c.m, c.n, it.k, c.alpha, vstride, nv));
             }
         }
         for (int o : order) {
             const OutBlock& ob = outs[o];
             p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 1.0f, tile_n);
         }
-        scratch_elems = std::max(scratch_elems, used);
-        tchunks.emplace_back(std::move(p1), std::move(p2));
-        i = j;
+        p1.order_tiles();
+        p2.order_tiles();
+        cfl[ch] = fl;
+    };
+    parallel_for(nch, build_chunk);
+    // merge the chunks' map tables (in chunk order) and renumber their segments
+    for (size_t ch = 0; ch < nch; ++ch) {
+        std::vector<int> gi(local[ch].keys.size());
+        for (size_t x = 0; x < gi.size(); ++x) gi[x] = maps.get(local[ch].keys[x]);
+        for (TmaWorkList* w : {&w1[ch], &w2[ch]})
+            for (TSeg& sg : w->segs) {
+                sg.a_map = gi[sg.a_map];
+                sg.b_map = gi[sg.b_map];
+            }
+        flops += cfl[ch];
+        scratch_elems = std::max(scratch_elems, plans[ch].used);
+        tchunks.emplace_back(std::move(w1[ch]), std::move(w2[ch]));
     }
     // the scratch's per-vector stride is now known
     scratch_elems = round_up(std::max<int64_t>(scratch_elems, 8), 8);

@@ -3,8 +3,11 @@
 #pragma once
 
 #include <array>
+#include <atomic>
+#include <exception>
 #include <map>
 #include <memory>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -14,6 +17,31 @@
 #include "symbolic.h"
 
 namespace dmrg {
+
+// fn(0 .. n-1) on up to 16 host threads; the first exception is rethrown
+template <typename Fn>
+void parallel_for(size_t n, const Fn& fn) {
+    const size_t nthr = std::min<size_t>(n, std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    if (nthr <= 1) {
+        for (size_t x = 0; x < n; ++x) fn(x);
+        return;
+    }
+    std::atomic<size_t> next{0};
+    std::vector<std::exception_ptr> err(nthr);
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < nthr; ++t)
+        pool.emplace_back([&, t]() {
+            try {
+                for (size_t x = next++; x < n; x = next++) fn(x);
+            } catch (...) {
+                err[t] = std::current_exception();
+            }
+        });
+    for (auto& th : pool) th.join();
+    for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+}
+
 
 // Block-sparse MPS kept on the host (source of truth for save / renormalise).
 struct MPSHost {

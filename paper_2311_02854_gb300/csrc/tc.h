@@ -72,6 +72,7 @@ struct TmaWorkList {
     // 128), split into K-chunks of at most kchunk (atomic modes only)
     void add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const std::vector<TSeg>& s, uint8_t mode,
                    int64_t kchunk, float alpha, int tn = 128);
+    void order_tiles();  // longest tiles first (stable)
     void upload(cudaStream_t st);
     void release();
 };
