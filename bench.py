@@ -410,6 +410,8 @@ def run_sigma_probe(args):
                       "sigma_flops": st["sigma_flops"], "tiles": st["sigma_tiles"], "stages": st["sigma_stages"],
                       "mma_flops": st["sigma_mma_flops"], "store_bytes": st["store_bytes"],
                       "tile_n": st["sigma_tile_n"], "kchunk": st["sigma_kchunk"],
+                      "load_bytes_phase1_other_scratch": st["sigma_load_bytes"][0],
+                      "load_bytes_phase2_other_scratch": st["sigma_load_bytes"][1],
                       "tune_candidates_ms": st["tune_cand_ms"], "tune_ms": st["ms_tune"]}), flush=True)
     plan.close()
 

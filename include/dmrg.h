@@ -152,6 +152,9 @@ typedef struct {
     double ms_tune;               /* wall time of all autotuner runs */
     double tune_cand_ms[4];       /* last autotuner run: sample time per candidate
                                      (128 / K-chunk, 64 / K-chunk, 128 / half K-chunk, 64 / half) */
+    double sigma_load_bytes[2][2];/* mixed sigma, one vector: operand bytes the tensor-core tiles
+                                     load through TMA, [phase 1 / 2][other operands / phase-1
+                                     scratch] (counts every box load, before any L2 reuse) */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

@@ -44,14 +44,13 @@ class Stats(C.Structure):
                 ("decim_nmat_last", C.c_int), ("decim_nmax_last", C.c_int), ("decim_sweeps32_last", C.c_int),
                 ("sigma_tile_n", C.c_int),
                 ("sigma_kchunk", C.c_int64), ("tunes", C.c_int64), ("tune_hits", C.c_int64), ("ms_tune", C.c_double),
-                ("tune_cand_ms", C.c_double * 4)]
+                ("tune_cand_ms", C.c_double * 4), ("sigma_load_bytes", (C.c_double * 2) * 2)]
 
     def as_dict(self):
-        d = {}
-        for f, _ in self._fields_:
-            v = getattr(self, f)
-            d[f] = list(v) if isinstance(v, C.Array) else v
-        return d
+        def conv(v):
+            return [conv(x) for x in v] if isinstance(v, C.Array) else v
+
+        return {f: conv(getattr(self, f)) for f, _ in self._fields_}
 
 
 def lib_path():

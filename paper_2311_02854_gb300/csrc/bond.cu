@@ -863,12 +863,18 @@ void set_bond(Plan& P, int k) {
         ProductList& tl = P.sigma_tc;
         tl.clear();
         tl.outs = pl.outs;
-        tl.cs = pl.cs;
-        for (Contrib& c : tl.cs) {
-            const Plan::Sector& s = P.layout[c.qsec];
-            c.Q.off = s.poff;
-            c.Q.ld = (int)round_up(s.dr, 8);
-        }
+        // the tensor-core list reads psi from its padded bf16 copy
+        tl.cs.resize(pl.cs.size());
+        const size_t cb = 1 << 16;
+        parallel_for((pl.cs.size() + cb - 1) / cb, [&](size_t b) {
+            for (size_t x = b * cb; x < std::min(pl.cs.size(), (b + 1) * cb); ++x) {
+                Contrib c = pl.cs[x];
+                const Plan::Sector& s = P.layout[c.qsec];
+                c.Q.off = s.poff;
+                c.Q.ld = (int)round_up(s.dr, 8);
+                tl.cs[x] = c;
+            }
+        });
         // vectors per launch (block Davidson passes up to n_roots at once)
         const int G = std::max(1, P.opt.n_roots);
         int64_t vs[kMaxBufs] = {};
@@ -884,7 +890,10 @@ void set_bond(Plan& P, int k) {
         P.stats.sigma_tile_n = shape.tn;
         P.stats.sigma_kchunk = shape.kchunk;
         tl.cs.clear();
-        for (int ph = 0; ph < 2; ++ph) P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
+        for (int ph = 0; ph < 2; ++ph) {
+            P.stats.sigma_tiles[ph] = P.stats.sigma_stages[ph] = 0;
+            P.stats.sigma_load_bytes[ph][0] = P.stats.sigma_load_bytes[ph][1] = 0.0;
+        }
         P.stats.sigma_mma_flops = 0.0;
         for (const auto& ch : tl.tchunks)
             for (int ph = 0; ph < 2; ++ph) {
@@ -895,6 +904,16 @@ void set_bond(Plan& P, int k) {
                     for (int q = t.seg_beg; q < t.seg_end; ++q) kk += round_up(w.segs[q].k, 16);
                     for (int q = t.seg_beg; q < t.seg_end; ++q) P.stats.sigma_stages[ph] += (w.segs[q].k + 63) / 64;
                     P.stats.sigma_mma_flops += 2.0 * 128 * 128 * (double)kk;
+                    // operand bytes the TMA loads for this tile (boxes of 128-byte
+                    // rows, one per piece), split into scratch and everything else
+                    const int nA = (t.m - t.m0 > 64) ? 2 : 1, nB = (std::min(t.tn, t.n - t.n0) > 64) ? 2 : 1;
+                    for (int q = t.seg_beg; q < t.seg_end; ++q) {
+                        const TSeg& g = w.segs[q];
+                        const double st = (double)((g.k + 63) / 64) * P.nsplit * 128.0;
+                        const double ba = st * nA * g.a_br, bb = st * nB * g.b_br;
+                        P.stats.sigma_load_bytes[ph][tl.maps.keys[g.a_map].buf == BUF_SCR ? 1 : 0] += ba;
+                        P.stats.sigma_load_bytes[ph][tl.maps.keys[g.b_map].buf == BUF_SCR ? 1 : 0] += bb;
+                    }
                 }
             }
         ensure_scratch(P, (int64_t)G * tl.scratch_elems);
@@ -936,51 +955,59 @@ void set_bond(Plan& P, int k) {
     {
         WorkList w;
         std::vector<std::vector<Seg>> per(P.layout.size());
-        std::vector<OpLookup> lcache(nbl), rcache(nbr);
-        for (const Term3& t : P.sp.terms) {
-            const LocalOp& M = Y.ops[t.y];
-            if (M.dq != QN(0, 0)) continue;
-            const int pR = ref_parity(R.lay, P.sp.interms, t.R);
-            for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
-            for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
-            for (size_t si = 0; si < P.layout.size(); ++si) {
-                const Plan::Sector& s = P.layout[si];
-                const double mv = M.at(s.y, s.y);
-                if (mv == 0.0) continue;
-                const OpLookup& ol = lcache[s.il];
-                if (!ol.ok || ol.j != s.il) continue;
-                const OpLookup& orr = rcache[s.ir];
-                if (!orr.ok || orr.j != s.ir) continue;
-                const int nl = L.lay.basis.qn[s.il].n;
-                const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
-                const int e = M.parity * nl + pR * (nl + ny);
-                const double zeta = (e & 1) ? -1.0 : 1.0;
-                View a = ol.v, b = orr.v;
-                if (a.ident) {
-                    a.buf = BUF_ID;
-                    a.off = 0;
-                    a.ld = P.ident_n;
+        // terms in blocks on host threads; each block's (sector, segment) pairs
+        // are appended in term order
+        std::vector<std::vector<std::pair<int, Seg>>> dpart(nblk);
+        parallel_for(nblk, [&](size_t blk) {
+            std::vector<OpLookup> lcache(nbl), rcache(nbr);
+            for (size_t ti = blk * tblk; ti < std::min(nterm, (blk + 1) * tblk); ++ti) {
+                const Term3& t = P.sp.terms[ti];
+                const LocalOp& M = Y.ops[t.y];
+                if (M.dq != QN(0, 0)) continue;
+                const int pR = ref_parity(R.lay, P.sp.interms, t.R);
+                for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
+                for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
+                for (size_t si = 0; si < P.layout.size(); ++si) {
+                    const Plan::Sector& s = P.layout[si];
+                    const double mv = M.at(s.y, s.y);
+                    if (mv == 0.0) continue;
+                    const OpLookup& ol = lcache[s.il];
+                    if (!ol.ok || ol.j != s.il) continue;
+                    const OpLookup& orr = rcache[s.ir];
+                    if (!orr.ok || orr.j != s.ir) continue;
+                    const int nl = L.lay.basis.qn[s.il].n;
+                    const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
+                    const int e = M.parity * nl + pR * (nl + ny);
+                    const double zeta = (e & 1) ? -1.0 : 1.0;
+                    View a = ol.v, b = orr.v;
+                    if (a.ident) {
+                        a.buf = BUF_ID;
+                        a.off = 0;
+                        a.ld = P.ident_n;
+                    }
+                    if (b.ident) {
+                        b.buf = BUF_ID;
+                        b.off = 0;
+                        b.ld = P.ident_n;
+                    }
+                    // diagonal as a (d x 1) column / (1 x d) row: stride ld + 1
+                    Seg sg{};
+                    sg.a_off = a.off;
+                    sg.lda = a.ld + 1;
+                    sg.a_tr = 0;
+                    sg.a_buf = (uint8_t)a.buf;
+                    sg.b_off = b.off;
+                    sg.ldb = b.ld + 1;
+                    sg.b_tr = 1;
+                    sg.b_buf = (uint8_t)b.buf;
+                    sg.k = 1;
+                    sg.alpha = t.c * zeta * mv;
+                    dpart[blk].push_back({(int)si, sg});
                 }
-                if (b.ident) {
-                    b.buf = BUF_ID;
-                    b.off = 0;
-                    b.ld = P.ident_n;
-                }
-                // diagonal as a (d x 1) column / (1 x d) row: stride ld + 1
-                Seg sg{};
-                sg.a_off = a.off;
-                sg.lda = a.ld + 1;
-                sg.a_tr = 0;
-                sg.a_buf = (uint8_t)a.buf;
-                sg.b_off = b.off;
-                sg.ldb = b.ld + 1;
-                sg.b_tr = 1;
-                sg.b_buf = (uint8_t)b.buf;
-                sg.k = 1;
-                sg.alpha = t.c * zeta * mv;
-                per[si].push_back(sg);
             }
-        }
+        });
+        for (auto& v : dpart)
+            for (auto& x : v) per[x.first].push_back(x.second);
         for (size_t si = 0; si < P.layout.size(); ++si) {
             const Plan::Sector& s = P.layout[si];
             w.add_block(s.off, BUF_OUT, s.dl, s.dr, s.dr, per[si], TILE_STORE);

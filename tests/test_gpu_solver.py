@@ -132,3 +132,44 @@ def test_k8_sweeps_vs_fci(tmp_path):
     e, w = plan.sweep(2)
     assert abs(e[-1] - efci) < 1e-10
     plan.close()
+
+
+@pytest.mark.parametrize("forward", [True, False])
+def test_decimation_two_stage_eigensolver(tmp_path, forward):
+    """Density-matrix blocks of 256 rows or more take the two-stage eigensolver
+    (FP32 sweeps, FP64 basis change and FP64 sweeps): discarded weight and the
+    next-bond guess against the oracle's dense FP64 decomposition."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    K, N, twoS, D, k = 14, 14, 0, 600, 7
+    Dcut = 300
+    h, L, mps, path = make_case(tmp_path, K, N, twoS, D, center=k, split="gaussian", wn=1.0, ws=1.0)
+    o = Oracle(h, eri_from_cholesky(L), N, twoS, mps)
+    ts = o.two_site(k)
+    psi = si.random_vector(ts.dim, seed=11)
+    w_ref, guess_ref = o.decimate_and_move(ts, k, psi[None], Dcut, forward)
+    g_ref = guess_ref[0]
+
+    plan = g.Plan(h, L, K, N, twoS, D, path)
+    plan.set_bond(k)
+    x = torch.from_numpy(psi.copy()).cuda()
+    cap = 4 * ts.dim
+    nxt = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    w, ndim = plan.decimate(x, 1, Dcut, forward, next_psi=nxt, next_cap=cap)
+    st = plan.stats()
+    print(f"K=14 D=600 -> {Dcut}: blocks {st['decim_nmat_last']}, largest {st['decim_nmax_last']}, "
+          f"sweeps FP32 {st['decim_sweeps32_last']} + FP64 {st['decim_sweeps_last']}, w {w:.15e} vs {w_ref:.15e}")
+    assert st["decim_nmax_last"] >= 256 and st["decim_sweeps32_last"] > 0
+    assert abs(w - w_ref) < 1e-12 * max(1.0, abs(w_ref))
+    gv = nxt[:ndim].cpu().numpy()
+    assert ndim == g_ref.size
+    # the guess is defined up to the gauge of the kept basis: compare its norm
+    # and its energy at the next bond
+    assert abs(gv @ gv - g_ref @ g_ref) < 1e-10
+    ts2 = o.two_site(k + 1 if forward else k - 1)
+    rq_ref = g_ref @ ts2.sigma(g_ref) / (g_ref @ g_ref)
+    gt = torch.from_numpy(gv.copy()).cuda()
+    sg = torch.empty_like(gt)
+    plan.sigma(gt, sg)
+    assert abs(float(gt @ sg) / float(gt @ gt) - rq_ref) < 1e-9
+    plan.close()
