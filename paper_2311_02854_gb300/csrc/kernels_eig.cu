@@ -197,13 +197,34 @@ __global__ void __launch_bounds__(NT) bj_rows(const BJMat<T>* __restrict__ mats,
         As[a * LD + b] = (col < n) ? pr.M.A[(int64_t)sub_index(pr, a) * n + col] : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < SB * SB; e += NT) {
-        const int a = e / SB, b = e % SB, col = tile * SB + b;
-        T acc = T(0);
-#pragma unroll 16
-        for (int k = 0; k < SB; ++k) acc = fma(Qs[k * LD + a], As[k * LD + b], acc);
-        if (col < n) pr.M.A[(int64_t)sub_index(pr, a) * n + col] = acc;
+    // 4 x 4 outputs per thread (rows ty + 16u, columns tx + 16w): 16 independent
+    // FMA chains and 8 shared loads per 16 FMAs
+    const int ty = tid / 16, tx = tid % 16;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < SB; ++k) {
+        T qa[4], ab[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            qa[u] = Qs[k * LD + ty + 16 * u];
+            ab[u] = As[k * LD + tx + 16 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] = fma(qa[u], ab[w], acc[u][w]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int a = ty + 16 * u, col = tile * SB + tx + 16 * w;
+            if (col < n) pr.M.A[(int64_t)sub_index(pr, a) * n + col] = acc[u][w];
+        }
 }
 
 // X[row tile, columns I u J] <- X[row tile, columns I u J] Q for X = A, then X = V
@@ -226,13 +247,33 @@ __global__ void __launch_bounds__(NT) bj_cols(const BJMat<T>* __restrict__ mats,
             As[a * LD + b] = (row < n) ? X[(int64_t)row * n + sub_index(pr, b)] : T(0);
         }
         __syncthreads();
-        for (int e = tid; e < SB * SB; e += NT) {
-            const int a = e / SB, b = e % SB, row = tile * SB + a;
-            T acc = T(0);
-#pragma unroll 16
-            for (int k = 0; k < SB; ++k) acc = fma(As[a * LD + k], Qs[k * LD + b], acc);
-            if (row < n) X[(int64_t)row * n + sub_index(pr, b)] = acc;
+        // 4 x 4 outputs per thread, as in bj_rows
+        const int ty = tid / 16, tx = tid % 16;
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+        for (int k = 0; k < SB; ++k) {
+            T xa[4], qb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xa[u] = As[(ty + 16 * u) * LD + k];
+                qb[u] = Qs[k * LD + tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fma(xa[u], qb[w], acc[u][w]);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int row = tile * SB + ty + 16 * u;
+                if (row < n) X[(int64_t)row * n + sub_index(pr, tx + 16 * w)] = acc[u][w];
+            }
         __syncthreads();
     }
 }
