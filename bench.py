@@ -207,11 +207,19 @@ def run_mine(args):
     setup_s = time.time() - t_setup
     st0 = plan.stats()
 
+    # wall time of the two calls of a step (both return with the stream idle)
+    wall = {"davidson": 0.0, "decimate_and_next_bond": 0.0}
+
     def bond_update(x, forward):
+        t0 = time.perf_counter()
         e, it, conv = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters, stream=stream)
+        t1 = time.perf_counter()
         cap = 4 * max(x.numel(), 1) + 64
         nxt = torch.zeros(cap, dtype=torch.float64, device="cuda")
         wdisc, nd = plan.decimate(x, 1, D, forward, next_psi=nxt, next_cap=cap, stream=stream)
+        t2 = time.perf_counter()
+        wall["davidson"] += t1 - t0
+        wall["decimate_and_next_bond"] += t2 - t1
         return nxt[:nd].clone(), e[0], it, wdisc
 
     # one step = one two-site bond update (set_bond: renormalisation, layout,
@@ -237,6 +245,8 @@ def run_mine(args):
     if world > 1:
         torch.distributed.barrier()
     s_before = plan.stats()
+    for key in wall:
+        wall[key] = 0.0
     clock = ClockSampler(local)
     clock.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -252,6 +262,13 @@ def run_mine(args):
     clocks = clock.stop()
     ms = ev0.elapsed_time(ev1)
     s_after = plan.stats()
+    wall_steps = {key: round(v / args.steps, 3) for key, v in wall.items()}
+    # the same counters' share of the timed steps (per step, seconds)
+    parts = {"sigma_device": (s_after["ms_sigma_dev"] - s_before["ms_sigma_dev"]) / 1e3 / args.steps,
+             "decimation_device": (s_after["ms_decim"] - s_before["ms_decim"]) / 1e3 / args.steps,
+             "renormalisation": (s_after["ms_renorm"] - s_before["ms_renorm"]) / 1e3 / args.steps,
+             "host_planning": (s_after["ms_host_plan"] - s_before["ms_host_plan"]) / 1e3 / args.steps,
+             "autotuner": (s_after["ms_tune"] - s_before["ms_tune"]) / 1e3 / args.steps}
     # sigma-only rate: one timed sigma call per vector size
     y = torch.empty_like(x)
     sig_ms = []
@@ -327,6 +344,8 @@ def run_mine(args):
         "decim_ms_total": round(st_end["ms_decim"], 1),
         "decim_ms_parts": {k: round(v, 1) for k, v in zip(("rho", "eigensolver", "host", "guess"),
                                                           st_end["ms_decim_parts"])},
+        "step_wall_s": wall_steps,
+        "step_parts_s": {key: round(v, 3) for key, v in parts.items()},
         "decim_sweeps_last": st_end["decim_sweeps_last"],
         "decim_conv_last": [float("%.3g" % c) for c in st_end["decim_conv_last"] if c > 0],
         "sigma_shape": {"tile_n": st_end["sigma_tile_n"], "kchunk": st_end["sigma_kchunk"],

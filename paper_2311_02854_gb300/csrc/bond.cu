@@ -1008,6 +1008,7 @@ void set_bond(Plan& P, int k) {
         });
         for (auto& v : dpart)
             for (auto& x : v) per[x.first].push_back(x.second);
+        w.rank1 = true;  // every segment is one diagonal outer product (k = 1)
         for (size_t si = 0; si < P.layout.size(); ++si) {
             const Plan::Sector& s = P.layout[si];
             w.add_block(s.off, BUF_OUT, s.dl, s.dr, s.dr, per[si], TILE_STORE);

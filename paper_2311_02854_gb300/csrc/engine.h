@@ -57,6 +57,7 @@ struct WorkList {
     Seg* d_segs = nullptr;
     size_t cap_tiles = 0, cap_segs = 0;
     double flops = 0.0;
+    bool rank1 = false;  // every segment has K = 1 (run by the rank-1 kernel)
     void clear() {
         tiles.clear();
         segs.clear();

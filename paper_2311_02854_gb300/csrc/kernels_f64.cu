@@ -201,6 +201,62 @@ __global__ void __launch_bounds__(NT) seg_gemm_f64_kernel(const Tile* __restrict
         }
     }
 }
+// The same product for lists whose segments all have K = 1 (rank-1 updates,
+// e.g. the diagonal of H_eff as sums of diag(O_L) diag(O_R)^T): each thread
+// reads its 4 + 4 operand elements straight from global memory (they stay in
+// L1 across the segments of a tile), no shared-memory staging or barriers.
+// Same accumulation order per element as seg_gemm_f64_kernel.
+__global__ void __launch_bounds__(NT) seg_outer_f64_kernel(const Tile* __restrict__ tiles,
+                                                           const Seg* __restrict__ segs, BufTable bt) {
+    const Tile T = tiles[blockIdx.x];
+    const int v = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int mrem = T.m - T.m0, nrem = T.n - T.n0;
+    for (int s = T.seg_beg; s < T.seg_end; ++s) {
+        const Seg S = segs[s];
+        int64_t A = S.a_off + (int64_t)v * bt.vstride[S.a_buf];
+        int64_t B = S.b_off + (int64_t)v * bt.vstride[S.b_buf];
+        A += S.a_tr ? (int64_t)T.m0 : (int64_t)T.m0 * S.lda;
+        B += S.b_tr ? (int64_t)T.n0 * S.ldb : (int64_t)T.n0;
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = ty + 16 * i;
+            a[i] = m < mrem ? ld_elem(bt, S.a_buf, A + (S.a_tr ? (int64_t)m : (int64_t)m * S.lda)) * S.alpha : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = tx + 16 * j;
+            b[j] = n < nrem ? ld_elem(bt, S.b_buf, B + (S.b_tr ? (int64_t)n * S.ldb : (int64_t)n)) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    double* C = bt.p[T.c_buf] + T.c_off + (int64_t)v * bt.vstride[T.c_buf];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = T.m0 + ty + 16 * i;
+        if (r >= T.m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = T.n0 + tx + 16 * j;
+            if (c >= T.n) continue;
+            double* dst = C + (int64_t)r * T.ldc + c;
+            if (T.mode == TILE_ATOMIC)
+                atomicAdd(dst, acc[i][j]);
+            else
+                *dst = acc[i][j];
+        }
+    }
+}
 }  // namespace
 
 void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaStream_t st) {
@@ -209,7 +265,10 @@ void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaSt
     const int64_t maxg = 2147483647LL;
     DMRG_REQUIRE(n <= maxg && nvec <= 65535, DMRG_EINVAL, "work list too large for one launch");
     dim3 grid((unsigned)n, (unsigned)nvec);
-    seg_gemm_f64_kernel<<<grid, NT, 0, st>>>(w.d_tiles, w.d_segs, bt);
+    if (w.rank1)
+        seg_outer_f64_kernel<<<grid, NT, 0, st>>>(w.d_tiles, w.d_segs, bt);
+    else
+        seg_gemm_f64_kernel<<<grid, NT, 0, st>>>(w.d_tiles, w.d_segs, bt);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
 }

@@ -131,7 +131,19 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
 
+    // wall time per phase (verbose): diagonal, orthogonalisation, sigma, Ritz
+    // step and residuals, preconditioner
+    double tph[5] = {0, 0, 0, 0, 0};
+    auto tnow = [&]() {
+        if (P.opt.verbose) DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return std::chrono::steady_clock::now();
+    };
+    auto tadd = [&](int i, std::chrono::steady_clock::time_point a) {
+        if (P.opt.verbose) tph[i] += std::chrono::duration<double, std::milli>(tnow() - a).count();
+    };
+    auto tp0 = tnow();
     hdiag(P, hd, st);
+    tadd(0, tp0);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(T, psi, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
     std::vector<double> G((size_t)ms * ms, 0.0);
     std::vector<double> theta(nr, 0.0), rnorm(nr, 0.0);
@@ -144,6 +156,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
     std::vector<int> order;
     while (true) {
         // orthonormalise the new directions (classical Gram-Schmidt, twice)
+        auto tp1 = tnow();
         int added = 0;
         for (int t = 0; t < nnew; ++t) {
             double* x = T + (int64_t)t * n;
@@ -185,8 +198,12 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
                 ++added;
             }
         }
+        tadd(1, tp1);
         if (added == 0) break;
+        auto tp2 = tnow();
         sigma(P, V + (int64_t)m * n, W + (int64_t)m * n, added, st);
+        tadd(2, tp2);
+        auto tp3 = tnow();
         for (int j = m; j < m + added; ++j) {
             dev_dots(V, n, m + added, W + (int64_t)j * n, n, dco, dwork, st);
             std::vector<double> col(m + added);
@@ -240,6 +257,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             }
             all = all && rnorm[i] <= tol;
         }
+        tadd(3, tp3);
         if (P.opt.verbose)
             fprintf(stderr, "[dmrg] davidson it=%d m=%d theta0=%.12f |r0|=%.3e\n", it, m, theta[0], rnorm[0]);
         if (all) {
@@ -257,6 +275,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             P.free(tjd, n);
         }
         // corrections: diagonal (Jacobi), or scaled per element by the learned g
+        auto tp4 = tnow();
         const bool use_mlp = precond == DMRG_PRECOND_MLP && P.mlp.trained && !P.harvest.on;
         if (use_mlp && P.n_mlp_feat < 6 * n) {
             if (P.d_mlp_feat) cudaFree(P.d_mlp_feat);
@@ -278,6 +297,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             }
         }
         if (precond == DMRG_PRECOND_MLP && !use_mlp) P.stats.precond_fallbacks += nr;
+        tadd(4, tp4);
         nnew = nr;
         if (m + nr > ms) {  // restart with the Ritz vectors
             DMRG_CHECK_CUDA(cudaMemcpyAsync(V, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
@@ -287,6 +307,10 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             m = nr;
         }
     }
+    if (P.opt.verbose)
+        fprintf(stderr, "[dmrg] davidson phases (ms): diagonal %.0f, orthogonalisation %.0f, sigma %.0f, "
+                        "Ritz+residual %.0f, preconditioner %.0f\n",
+                tph[0], tph[1], tph[2], tph[3], tph[4]);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(psi, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
     if (P.mixed() && P.opt.fp64_final) {
         // FP64 Rayleigh quotients <x|H|x> of the mixed-precision Ritz vectors
