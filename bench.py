@@ -178,6 +178,19 @@ def sample_flops():
     return f
 
 
+def max_over_ranks(x, world):
+    """Max of x over the ranks of the process group (x itself on one rank):
+    the job's time is that of its slowest replica."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # own arm
 # ---------------------------------------------------------------------------
@@ -287,11 +300,7 @@ def run_mine(args):
     # count of the bond current at the end is used) plus renormalisations
     renorm_fl = s_after["renorm_flops_last"]
     step_flops = n_sig * sigma_flops + args.steps * (renorm_fl + s_after["interm_flops"])
-    max_ms = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        max_ms = float(t.item())
+    max_ms = max_over_ranks(ms, world)
     value = world * step_flops / (max_ms / 1e3) / 1e12
     sig_t = statistics.median(sig_ms)
     sigma_tflops = sigma_flops / (sig_t / 1e3) / 1e12
