@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(NT) bj_store(const BJMat<double>* __restrict__
 // off/|A| <= tol, or the decrease of a sweep is below `stall` (factor), or
 // max_sweeps; returns the sweeps run; hist gets off/|A| before each sweep
 template <typename T>
-int bj_sweeps(const BJMat<T>* d_mats, const std::vector<BJMat<T>>& mats, const int* d_off, int nmat, int njob,
+int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
               int ne_max, int ntile, T* Qall, double* d_norm, int max_sweeps, double tol, double stall,
               double stall_from, cudaStream_t st, std::vector<double>* hist, double* final_worst) {
     const size_t smem = 2 * SB * LD * sizeof(T);
@@ -457,7 +457,6 @@ int bj_sweeps(const BJMat<T>* d_mats, const std::vector<BJMat<T>>& mats, const i
         DMRG_CHECK_CUDA(cudaGetLastError());
         ++sweeps;
     }
-    (void)mats;
     return sweeps;
 }
 
@@ -558,7 +557,7 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
     if (two_stage) {
         DMRG_CHECK_CUDA(cudaMemcpyAsync(d_m32, m32.data(), sizeof(BJMat<float>) * nmat, cudaMemcpyHostToDevice, st));
         // stage 1: FP32 sweeps down to the FP32 rounding level
-        const int s32 = bj_sweeps<float>(d_m32, m32, d_off, nmat, njob, ne_max, ntile, (float*)Qall, d_norm,
+        const int s32 = bj_sweeps<float>(d_m32, d_off, nmat, njob, ne_max, ntile, (float*)Qall, d_norm,
                                          kMaxSweeps32, kTol32, kStall32, kStallFrom32, st, hist, &worst);
         if (sweeps32_out) *sweeps32_out = s32;
         // stage 2 (FP64): V = V32 made orthonormal by two Newton-Schulz steps
@@ -591,7 +590,7 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
         ++launch_counter();
     }
     // FP64 sweeps to the tolerance
-    const int sweeps = bj_sweeps<double>(d_mats, mats, d_off, nmat, njob, ne_max, ntile, Qall, d_norm, max_sweeps, tol,
+    const int sweeps = bj_sweeps<double>(d_mats, d_off, nmat, njob, ne_max, ntile, Qall, d_norm, max_sweeps, tol,
                                          kStall64, kStallFrom64, st, hist, &worst);
     bj_store<<<dim3(gx, nmat), NT, 0, st>>>(d_mats, d_jobs);
     ++launch_counter();
