@@ -15,7 +15,7 @@ blocks       block-sparse operators, the local basis, the normal and
 sigma        the two-site sigma vector of Eq. (Sigma) and the diagonal of H_eff
 dmrg         environments, Davidson, decimation and the two-dot sweep
 
-Conventions (the paper leaves them implicit; see DESIGN.md "readings"):
+Conventions (the paper leaves them implicit):
 spin orbital p = 2*i + s (s = 0 alpha, 1 beta), Jordan-Wigner order
 (1a, 1b, 2a, 2b, ...); local basis {vac, b, a, ab} with |ab> = a+_a a+_b |vac>;
 <pq|rs> = (i_p i_r | i_q i_s) delta(s_p, s_r) delta(s_q, s_s) and
