@@ -241,6 +241,20 @@ dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi_dev, int n_roots, 
 dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, double* energies,
                        double* discarded, void* stream);
 
+/* Linear extrapolation of energies to zero discarded weight (Tab. energy and
+ * Fig. extrapolation: E(w) = A w + E_{w=0}, fitted by least squares over a
+ * series of runs, e.g. the energies and discarded weights that dmrg_sweep
+ * returns for a D schedule).
+ *  w, E    n host values each: discarded weights and energies (Eh); read only.
+ *  n       number of points, >= 2.
+ *  e0      out: E_{w=0}, the intercept.
+ *  slope   out (may be NULL): A.
+ *  rms     out (may be NULL): root-mean-square residual of the fit.
+ * Host arithmetic only: no plan, no device work, callable without a GPU.
+ * DMRG_EINVAL for n < 2, a NULL w / E / e0, non-finite values, or weights that
+ * are all equal. */
+dmrg_status dmrg_extrapolate(const double* w, const double* E, int n, double* e0, double* slope, double* rms);
+
 /* Write the current MPS (same format as the input file). */
 dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path);
 

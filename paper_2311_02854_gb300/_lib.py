@@ -93,6 +93,7 @@ _SIGS = {
     "dmrg_mlp_gradient": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "dmrg_mlp_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "dmrg_mlp_num_params": (C.c_int, []),
+    "dmrg_extrapolate": (C.c_int, [_D, _D, C.c_int, _D, _D, _D]),
 }
 
 
@@ -345,6 +346,20 @@ def grouped_gemm_noalloc(blocks, a, b, c, stream=None):
     code = lib().dmrg_grouped_gemm_noalloc(len(ms), *ptrs, alpha.ctypes.data_as(_D), _ptr(a), _ptr(b), _ptr(c),
                                            _stream(stream))
     _check(code, None)
+
+
+def extrapolate(w, E):
+    """dmrg_extrapolate: least-squares line E = A w + E0 through a series of
+    (discarded weight, energy) points; returns (E0, A, rms residual).  Host
+    arithmetic in the library (no GPU needed)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    if w.shape != E.shape or w.ndim != 1:
+        raise ValueError("w and E must be 1-D and equally long")
+    e0, a, r = C.c_double(), C.c_double(), C.c_double()
+    code = lib().dmrg_extrapolate(_dptr(w), _dptr(E), int(w.size), C.pointer(e0), C.pointer(a), C.pointer(r))
+    _check(code, None)
+    return e0.value, a.value, r.value
 
 
 def noalloc_scratch_bytes():

@@ -484,6 +484,39 @@ dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, do
     });
 }
 
+dmrg_status dmrg_extrapolate(const double* w, const double* E, int n, double* e0, double* slope, double* rms) {
+    if (!w || !E || !e0 || n < 2) return fail(nullptr, DMRG_EINVAL, "extrapolation needs two points and outputs");
+    // centred two-pass least squares: mean, then the centred moments
+    double mw = 0.0, mE = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(w[i]) || !std::isfinite(E[i]))
+            return fail(nullptr, DMRG_EINVAL, "non-finite point in the extrapolation series");
+        mw += w[i];
+        mE += E[i];
+    }
+    mw /= n;
+    mE /= n;
+    double sxx = 0.0, sxy = 0.0;
+    for (int i = 0; i < n; ++i) {
+        sxx += (w[i] - mw) * (w[i] - mw);
+        sxy += (w[i] - mw) * (E[i] - mE);
+    }
+    if (!(sxx > 0.0)) return fail(nullptr, DMRG_EINVAL, "all discarded weights are equal");
+    const double a = sxy / sxx;
+    const double b = mE - a * mw;
+    *e0 = b;
+    if (slope) *slope = a;
+    if (rms) {
+        double r2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double r = E[i] - (a * w[i] + b);
+            r2 += r * r;
+        }
+        *rms = std::sqrt(r2 / n);
+    }
+    return DMRG_OK;
+}
+
 dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path) {
     if (!plan || !path) return fail(plan, DMRG_EINVAL, "bad arguments");
     if (!plan->P.mps.write(path)) return fail(plan, DMRG_EIO, std::string("cannot write ") + path);
