@@ -246,10 +246,6 @@ def run_mine(args):
         direction[0] = not fwd
         return x, (e,), it
 
-    def flops_now():
-        s = plan.stats()
-        return s
-
     # warm-up
     x = psi
     for _ in range(args.warmup):

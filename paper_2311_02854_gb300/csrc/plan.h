@@ -50,7 +50,6 @@ struct MPSHost {
     std::vector<std::map<std::array<int, 3>, std::vector<double>>> sites;      // (il, n, ir) -> d_l x d_r
     bool read(const std::string& path, std::string& err);
     bool write(const std::string& path) const;
-    int bond_dim(int b, int i) const { return bonds[b][i][2]; }
 };
 
 // Operand view of a dense matrix stored in buffer `buf`: element (i, j) at
