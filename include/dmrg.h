@@ -347,8 +347,12 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
  * with DMRG_EINVAL and a message giving the size needed.  No device memory is
  * allocated or freed.
  *
- * The call is asynchronous on `stream` (launch errors are returned; faults
- * surface at the caller's next synchronisation).  The first call on a device
+ * The kernel runs asynchronously on `stream` (launch errors are returned;
+ * faults surface at the caller's next synchronisation), but the work list is
+ * copied from pageable host memory, which may make the call wait for the
+ * stream's earlier work before it returns.  Because that host copy does not
+ * outlive the call, a stream that is being captured is refused with
+ * DMRG_EINVAL before anything is enqueued.  The first call on a device
  * looks up the array's device address with that device current (with lazy
  * module loading the driver also places the array in device memory at that
  * point); make it before any stream capture begins.  All calls share the one array: calls on

@@ -66,6 +66,13 @@ void grouped_gemm_f64_noalloc(const WorkList& host_wl, const double* a, const do
                                      std::to_string(kScratchBytes) + " (" + std::to_string(sizeof(Tile)) +
                                      " bytes per 64x64 output tile, " + std::to_string(sizeof(Seg)) +
                                      " per segment)");
+    // The work list is copied from host memory that is freed when the call
+    // returns; a captured copy would replay from that dead pointer, so a
+    // stream under capture is refused before anything is enqueued.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DMRG_CHECK_CUDA(cudaStreamIsCapturing(st, &cap));
+    DMRG_REQUIRE(cap == cudaStreamCaptureStatusNone, DMRG_EINVAL,
+                 "dmrg_grouped_gemm_noalloc called on a stream that is being captured");
     unsigned char* base = scratch_for_current_device();
     DMRG_CHECK_CUDA(cudaMemcpyAsync(base, host_wl.tiles.data(), tile_bytes, cudaMemcpyHostToDevice, st));
     if (seg_bytes > 0)

@@ -97,3 +97,34 @@ def test_noalloc_rejects_work_list_beyond_static_array():
     with pytest.raises(g.DMRGError) as exc:
         g.grouped_gemm_noalloc(blocks, dA, dB, dC)
     assert exc.value.code == -1 and "static scratch" in str(exc.value)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The work list is copied from host memory that the call frees on return,
+    so a graph captured around the call would replay a dead host pointer.  A
+    stream under capture is refused before anything is enqueued, and the
+    entry point keeps working afterwards."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    A, B, blocks, ref, ctot = _problem(13, 4)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.zeros(ctot, dtype=torch.float64, device="cuda")
+    g.grouped_gemm_noalloc(blocks, dA, dB, dC)  # set-up outside any capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.stream(s):
+        graph.capture_begin(capture_error_mode="thread_local")
+        try:
+            g.grouped_gemm_noalloc(blocks, dA, dB, dC, stream=s)
+        except g.DMRGError as e:
+            code = e.code
+        finally:
+            graph.capture_end()
+    assert code == -1
+    dC.zero_()
+    g.grouped_gemm_noalloc(blocks, dA, dB, dC)
+    got = dC.cpu().numpy()
+    for off, m, n, C in ref:
+        np.testing.assert_allclose(got[off:off + m * n].reshape(m, n), C, rtol=1e-12, atol=1e-12)
