@@ -172,8 +172,10 @@ class Oracle:
 
 def decimate(layout, X, left_labels, right_labels, D, forward, cutoff=1e-14):
     """Group the two-site vectors X (n_roots x dim) by the label q of the bond
-    between the two sites, M_q[(il c1), (c2 ir)]; keep the D largest singular
-    values (state-averaged density matrix eigenvalues for several roots)."""
+    between the two sites, M_q[(il c1), (c2 ir)]; for one root take the SVD of
+    every M_q and keep the D largest singular values s > cutoff (weights s^2);
+    for several roots the eigenvalues of the state-averaged density matrix,
+    kept above cutoff^2.  Ties break by sector order, then index."""
     groups = {}
     for (il, c1, c2, ir, off, dl, dr) in layout:
         ql = left_labels[il]
@@ -202,11 +204,18 @@ def decimate(layout, X, left_labels, right_labels, D, forward, cutoff=1e-14):
                 M[ro:ro + dl, co:co + dr] = X[v, off:off + dl * dr].reshape(dl, dr)
             mats.append(M)
         g["mats"] = mats
-        if forward:
-            rho = sum(M @ M.T for M in mats) / nvec
+        if nvec == 1:
+            # one root: singular values of M_q (their squares are the weights);
+            # left vectors for the forward move, right vectors backward
+            U, s, Vt = np.linalg.svd(mats[0], full_matrices=False)
+            lam, vec = s * s, (U if forward else Vt.T)
         else:
-            rho = sum(M.T @ M for M in mats) / nvec
-        lam, vec = np.linalg.eigh(rho)
+            # several roots: state-averaged density matrix, equal weights
+            if forward:
+                rho = sum(M @ M.T for M in mats) / nvec
+            else:
+                rho = sum(M.T @ M for M in mats) / nvec
+            lam, vec = np.linalg.eigh(rho)
         order = np.argsort(-lam, kind="stable")
         lam, vec = lam[order], vec[:, order]
         decomp[q] = (lam, vec)

@@ -88,3 +88,49 @@ def test_full_D_sweep_k8():
     mps = si.random_mps(K, N, twoS, bonds, center=1, seed=2)
     E, w, be = Oracle(h, eri, N, twoS, mps).sweep(2, 256, tol=1e-8)
     assert abs(E[-1] - efci) < 1e-10
+
+
+def _group_with_singular_values(s, forward, seed=5):
+    """One quantum-number group whose matrix M_q has the singular values s
+    (two column blocks forward, two row blocks backward), as a layout + vector."""
+    rng = np.random.default_rng(seed)
+    nr, nc = (6, 9) if forward else (9, 6)
+    U, _ = np.linalg.qr(rng.standard_normal((nr, nr)))
+    V, _ = np.linalg.qr(rng.standard_normal((nc, nc)))
+    r = len(s)
+    M = (U[:, :r] * s) @ V[:, :r].T
+    if forward:
+        # left sector 0 with c1 = 0 (label (0,0)); column components (c2, ir) = (0, 0), (1, 1)
+        layout = [(0, 0, 0, 0, 0, 6, 5), (0, 0, 1, 1, 30, 6, 4)]
+        psi = np.concatenate([M[:, :5].ravel(), M[:, 5:].ravel()])
+        left, right = [(0, 0)], [(0, 0), (1, -1)]
+    else:
+        # right sector 0 with c2 = 0; row components (il, c1) = (0, 0), (1, 0)
+        layout = [(0, 0, 0, 0, 0, 5, 6), (1, 0, 0, 0, 30, 4, 6)]
+        psi = np.concatenate([M[:5].ravel(), M[5:].ravel()])
+        left, right = [(0, 0), (0, 0)], [(0, 0)]
+    return layout, psi, left, right, M
+
+
+@pytest.mark.parametrize("forward", [True, False])
+def test_decimation_near_null_singular_values_match_svd(forward):
+    """One root: the weights are the squared singular values of M_q, including
+    values far below the rounding floor of a density-matrix eigensolver
+    (1e-10, 1e-13), and exactly singular directions are dropped (s <= 1e-14)."""
+    s = np.array([1.0, 0.5, 1e-3, 1e-10, 1e-13])  # rank 5 of 6: one exact zero
+    layout, psi, left, right, M = _group_with_singular_values(s, forward)
+    groups, kept, w = decimate(layout, psi[None, :], left, right, 10, forward)
+    assert len(kept) == 1
+    q, vec, _ = kept[0]
+    assert vec.shape[1] == 5  # the exactly singular direction is not kept
+    ref = np.linalg.svd(M, compute_uv=False)
+    assert abs(ref[5]) < 1e-14
+    assert w < 1e-28
+    # the kept vectors span the leading singular subspace of M_q
+    Uref, sref, Vtref = np.linalg.svd(M)
+    basis = Uref[:, :5] if forward else Vtref[:5].T
+    np.testing.assert_allclose(np.abs(vec.T @ basis), np.eye(5), atol=1e-6)
+    # truncation to D = 2: the discarded weight is the sum of the dropped s^2
+    _, kept2, w2 = decimate(layout, psi[None, :], left, right, 2, forward)
+    assert kept2[0][1].shape[1] == 2
+    assert abs(w2 - np.sum(s[2:] ** 2)) < 1e-18
