@@ -2,12 +2,15 @@
 renormalisation) on seeded synthetic inputs shaped like the K=73 / N=114
 active space, at bond dimension D=3000.
 
-One step = two bond updates at the middle of the chain: Davidson at bond
-(k, k+1) with the mixed-precision sigma, decimation to D with renormalisation
-of the grown left block, Davidson at (k+1, k+2), decimation back.  Reported
-value: algorithmic TFLOP/s of the step (sigma + renormalisation + intermediate
-products / device time of the step); sigma alone, seconds per site and the
-end-to-end rate (host buffers, copies in the timed region) ride along.
+One step = one two-site bond update at the middle of the chain: Davidson at
+the current bond (mixed-precision sigma; optionally the FP64 residual
+correction), decimation to D, renormalisation of the grown block and the
+planning of the next bond; steps alternate between moving forward and back.
+Reported value: algorithmic TFLOP/s of the timed steps (every sigma call at its
+own bond's planned count, FP64-accurate sigma calls, renormalisations and
+intermediates, from the library's counters) over their device time; seconds
+per site, sigma alone, Davidson convergence and the end-to-end rate through
+the host-buffer C-ABI call ride along.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 """
@@ -37,7 +40,7 @@ WORKLOADS = {
     "k54_d2000": dict(K=54, N=54, twoS=0, D=2000, n_chol=216, ell=3.0, h_min=-4.0, wn=1.45, ws=1.45),
 }
 METRIC = "sigma=H*psi TFLOP/s, s/site at K=73,D=3000; mixed vs FP64 at dE<=1e-6 Eh"
-PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2, "bf16x6": 3}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16": 2, "bf16x6": 3, "fp64tc": 4}
 # bounded sample the CPU oracle runs for the baseline (same recipe, small K)
 CPU_SAMPLE = dict(K=14, N=14, twoS=0, D=600, n_chol=56, ell=3.0, h_min=-4.0, wn=1.0, ws=1.0)
 
@@ -109,23 +112,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM traffic of one middle-bond sigma call of a workload (dram__bytes_read.sum +
-# dram__bytes_write.sum summed over the tensor-core launches of the call, from an
-# ncu capture of `bench.py --sigma-only`), with the tensor-core K stages of that
-# call.  The traffic of a sigma call in the timed steps is taken in proportion to
-# its stages; it is reported only while the kernel source is the one captured.
-SIGMA_TRAFFIC = {
-    "k73_d3000:bf16x3": dict(bytes=1416.604e9 + 245.834e9, stages=33096283 + 31440895,
-                             kernel_sha256="7e607aea19e15606cd3ad47b6db602e73418b24d046e9deef4d20ade31b169cd"),
-}
-
-
-def kernel_sha256():
-    import hashlib
-    with open(os.path.join(ROOT, "paper_2311_02854_gb300", "csrc", "kernels_tc.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
-
-
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -139,8 +125,10 @@ def measured_peaks():
 # CPU oracle baseline (bounded sample of the same recipe)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(n_sigma=3, flops=None):
-    """Time the CPU oracle's sigma on the bounded sample; returns (TFLOP/s, seconds, cores)."""
+def oracle_sample_rate(n_sigma=3):
+    """Time the CPU oracle's sigma on the bounded sample.  Returns (TFLOP/s,
+    seconds per sigma, threads): the FLOPs are those of the oracle's own
+    products (its term loop counts them), so no part of the library runs here."""
     from oracle.dmrg import Oracle
     from oracle.hamiltonian import eri_from_cholesky
     w = CPU_SAMPLE
@@ -152,8 +140,10 @@ def oracle_sample_rate(n_sigma=3, flops=None):
     psi = si.random_vector(ts.dim, seed=1)
     ts.sigma(psi)  # builds the term list once
     t0 = time.perf_counter()
+    fl = 0
     for _ in range(n_sigma):
         ts.sigma(psi)
+        fl += ts.flops_last
     dt = (time.perf_counter() - t0) / n_sigma
     cores = os.cpu_count()
     try:
@@ -161,21 +151,7 @@ def oracle_sample_rate(n_sigma=3, flops=None):
         cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) or cores
     except Exception:
         pass
-    return (flops / dt / 1e12 if flops else None), dt, cores
-
-
-def sample_flops():
-    """Algorithmic sigma FLOPs of the bounded sample (the library's planner count)."""
-    import paper_2311_02854_gb300 as g
-    w = CPU_SAMPLE
-    k = w["K"] // 2
-    with tempfile.TemporaryDirectory() as td:
-        h, L, bonds, path = make_inputs(w, td, k)
-        plan = g.Plan(h, L, w["K"], w["N"], w["twoS"], w["D"], path, precision=0)
-        plan.set_bond(k)
-        f = plan.stats()["sigma_flops"]
-        plan.close()
-    return f
+    return fl / n_sigma / dt / 1e12, dt, cores
 
 
 def max_over_ranks(x, world):
@@ -212,20 +188,23 @@ def run_mine(args):
     td = tempfile.mkdtemp(prefix="dmrg_bench_")
     h, L, bonds, path = make_inputs(w, td, k)
     plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=prec, tol=args.tol, max_iter=args.dav_iters,
-                  keep_envs=0)
+                  keep_envs=0, fp64_store=int(args.fp64_store), refine=int(args.refine),
+                  fp64_tc=int(args.fp64_tc))
     stream = torch.cuda.Stream()
     plan.set_bond(k, stream=stream)
     dim = plan.dim
     psi = torch.from_numpy(si.random_vector(dim, seed=1)).cuda()
     setup_s = time.time() - t_setup
-    st0 = plan.stats()
 
     # wall time of the two calls of a step (both return with the stream idle)
     wall = {"davidson": 0.0, "decimate_and_next_bond": 0.0}
+    dav = []  # per step: iterations, converged, stalled, residual, correction rounds
 
     def bond_update(x, forward):
         t0 = time.perf_counter()
         e, it, conv = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters, stream=stream)
+        st = plan.stats()
+        dav.append((it, conv, st["davidson_stalled_last"], st["davidson_rnorm_last"], st["davidson_refine_last"]))
         t1 = time.perf_counter()
         cap = 4 * max(x.numel(), 1) + 64
         nxt = torch.zeros(cap, dtype=torch.float64, device="cuda")
@@ -235,50 +214,62 @@ def run_mine(args):
         wall["decimate_and_next_bond"] += t2 - t1
         return nxt[:nd].clone(), e[0], it, wdisc
 
-    # one step = one two-site bond update (set_bond: renormalisation, layout,
-    # intermediates, work lists; Davidson; decimation), alternating between
-    # the middle bond moving forward and the next bond moving back
+    # one step = one two-site bond update (Davidson, decimation with the
+    # renormalisation of the grown block, layout, intermediates and work lists
+    # of the next bond), alternating between the middle bond moving forward
+    # and the next bond moving back
     direction = [True]
 
     def step(x):
         fwd = direction[0]
         x, e, it, wd = bond_update(x, fwd)
         direction[0] = not fwd
-        return x, (e,), it
+        return x, e
 
-    # warm-up
+    def flop_counters(st):
+        return (st["sigma_flops_dev"] + st["sigma_acc_flops"] + st["renorm_flops_total"]
+                + st["interm_flops_total"])
+
     x = psi
     for _ in range(args.warmup):
-        x, _, _ = step(x)
+        x, _ = step(x)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     s_before = plan.stats()
     for key in wall:
         wall[key] = 0.0
+    dav.clear()
     clock = ClockSampler(local)
     clock.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    energies, iters = [], 0
+    energies = []
     for _ in range(args.steps):
-        x, e, it = step(x)
+        x, e = step(x)
         energies.append(e)
-        iters += it
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = clock.stop()
     ms = ev0.elapsed_time(ev1)
     s_after = plan.stats()
+    dav_timed = list(dav)
     wall_steps = {key: round(v / args.steps, 3) for key, v in wall.items()}
     # the same counters' share of the timed steps (per step, seconds)
     parts = {"sigma_device": (s_after["ms_sigma_dev"] - s_before["ms_sigma_dev"]) / 1e3 / args.steps,
+             "fp64_sigma_device": (s_after["ms_sigma_acc"] - s_before["ms_sigma_acc"]) / 1e3 / args.steps,
              "decimation_device": (s_after["ms_decim"] - s_before["ms_decim"]) / 1e3 / args.steps,
              "renormalisation": (s_after["ms_renorm"] - s_before["ms_renorm"]) / 1e3 / args.steps,
              "host_planning": (s_after["ms_host_plan"] - s_before["ms_host_plan"]) / 1e3 / args.steps,
              "autotuner": (s_after["ms_tune"] - s_before["ms_tune"]) / 1e3 / args.steps}
-    # sigma-only rate: one timed sigma call per vector size
+    # algorithmic FLOPs of the timed steps, from the library's counters: every
+    # sigma call (each counted at its own bond's planned count), FP64-accurate
+    # sigma calls, renormalisations and intermediates
+    step_flops = flop_counters(s_after) - flop_counters(s_before)
+    max_ms = max_over_ranks(ms, world)
+    value = world * step_flops / (max_ms / 1e3) / 1e12
+    # sigma alone at the bond current after the timed steps (CUDA events)
     y = torch.empty_like(x)
     sig_ms = []
     for _ in range(3):
@@ -289,17 +280,8 @@ def run_mine(args):
         torch.cuda.synchronize()
         sig_ms.append(e0.elapsed_time(e1))
     s_sig = plan.stats()
-    sigma_flops = s_sig["sigma_flops"]
-    n_sig = s_after["sigma_calls"] - s_before["sigma_calls"]
-    # algorithmic FLOPs of the timed steps: sigma calls at the two bonds (both
-    # middle bonds have the same planned count to within a few percent; the
-    # count of the bond current at the end is used) plus renormalisations
-    renorm_fl = s_after["renorm_flops_last"]
-    step_flops = n_sig * sigma_flops + args.steps * (renorm_fl + s_after["interm_flops"])
-    max_ms = max_over_ranks(ms, world)
-    value = world * step_flops / (max_ms / 1e3) / 1e12
     sig_t = statistics.median(sig_ms)
-    sigma_tflops = sigma_flops / (sig_t / 1e3) / 1e12
+    sigma_tflops = s_sig["sigma_flops"] / (sig_t / 1e3) / 1e12
     peaks, src = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     # roofline of the dominant kernel from the sigma calls of the timed steps:
@@ -308,25 +290,36 @@ def run_mine(args):
     d_ms = s_after["ms_sigma_dev"] - s_before["ms_sigma_dev"]
     d_n = s_after["sigma_timed"] - s_before["sigma_timed"]
     achieved = (s_after["sigma_flops_dev"] - s_before["sigma_flops_dev"]) / (d_ms / 1e3) / 1e12 if d_ms > 0 else 0.0
-    traffic = None
-    tr = SIGMA_TRAFFIC.get(f"{args.workload}:{args.precision}")
-    if tr and d_n > 0 and kernel_sha256() == tr["kernel_sha256"]:
-        traffic = int(tr["bytes"] / tr["stages"] * (s_after["sigma_stages_dev"] - s_before["sigma_stages_dev"]) / d_n)
-    # end-to-end: the same step with the guess from pinned host memory and the
-    # final vector read back every step
-    host_in = torch.from_numpy(x.cpu().numpy()).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    # end-to-end through the host-buffer C-ABI call: each step copies its guess
+    # from pinned host memory, runs Davidson and the decimation, and reads the
+    # next bond's guess back into pinned host memory
+    n_e2e = max(3, args.e2e_steps)
+    cap = 4 * x.numel() + 64
+    hbuf = [torch.empty(cap, dtype=torch.float64).pin_memory(), torch.empty(cap, dtype=torch.float64).pin_memory()]
+    hbuf[0][:x.numel()].copy_(x.cpu())
+    cur = x.numel()
+    h2d = d2h = 0
+    s_e0 = plan.stats()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    xe = None
-    for _ in range(max(1, args.e2e_steps)):
-        xe = host_in.to("cuda", non_blocking=True)
-        xe, _, _ = step(xe)
-        host_out = xe.to("cpu")
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / max(1, args.e2e_steps)
-    e2e_value = world * (step_flops / args.steps) / e2e_s / 1e12
+    for i in range(n_e2e):
+        src_h, dst_h = hbuf[i % 2].numpy(), hbuf[(i + 1) % 2].numpy()
+        fwd = direction[0]
+        e, it, wd, nd, conv = plan.update_bond_host(src_h[:cur], 1, D, fwd, next_psi=dst_h, stream=stream)
+        direction[0] = not fwd
+        h2d += cur * 8
+        d2h += nd * 8
+        cur = nd
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    s_e1 = plan.stats()
+    e2e_flops = (flop_counters(s_e1) - flop_counters(s_e0)) / n_e2e
+    e2e_value = world * e2e_flops / e2e_s / 1e12
     st_end = plan.stats()
     launches = s_after["kernel_launches"] - s_before["kernel_launches"]
+    n_conv = sum(1 for d in dav_timed if d[1])
+    mode = args.precision + (" + FP64 store" if args.fp64_store else "") + (
+        " (FP64 products on the tensor-core engine)" if args.fp64_tc else "") + (
+        " + FP64 residual correction" if args.refine else "")
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
@@ -335,50 +328,49 @@ def run_mine(args):
                                f"middle bond {k}, Gaussian sector split (widths {w['wn']}), seeded",
                    "global_batch": world, "seq_len": D, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (operator store ~%.1f GB)" % (st_end["store_bytes"] / 1e9),
-                   "step": "1 bond update (renormalisation, intermediates, Davidson <= %d sigma, decimation)" % args.dav_iters},
+                   "mode": mode,
+                   "step": ("1 bond update: Davidson (tol %.0e, <= %d iterations, stops early when the mixed "
+                            "residual stalls), decimation, renormalisation, intermediates and work lists of the "
+                            "next bond" % (args.tol, args.dav_iters))},
         "s_per_site": round(max_ms / 1e3 / args.steps, 4),
         "sigma_tflops": round(sigma_tflops, 3),
         "sigma_ms": round(sig_t, 3),
-        "sigma_flops": sigma_flops,
-        "davidson_iters_per_step": iters / args.steps,
-        "energies": [list(map(float, e)) for e in energies],
+        "sigma_flops_end_bond": s_sig["sigma_flops"],
+        "step_flops": step_flops / args.steps,
+        "davidson": {"iters_per_step": sum(d[0] for d in dav_timed) / max(len(dav_timed), 1),
+                     "converged_steps": n_conv, "stalled_steps": sum(1 for d in dav_timed if d[2]),
+                     "residual_max": max((d[3] for d in dav_timed), default=None),
+                     "residual_per_step": [float("%.3g" % d[3]) for d in dav_timed],
+                     "correction_rounds": [d[4] for d in dav_timed]},
+        "energies": [float(e) for e in energies],
         "setup_s": round(setup_s, 1),
-        "host_plan_ms_total": round(st_end["ms_host_plan"], 1),
-        "renorm_ms_total": round(st_end["ms_renorm"], 1),
-        "davidson_ms_total": round(st_end["ms_davidson"], 1),
-        "decim_ms_total": round(st_end["ms_decim"], 1),
-        "decim_ms_parts": {k: round(v, 1) for k, v in zip(("rho", "eigensolver", "host", "guess"),
-                                                          st_end["ms_decim_parts"])},
         "step_wall_s": wall_steps,
         "step_parts_s": {key: round(v, 3) for key, v in parts.items()},
-        "decim_sweeps_last": st_end["decim_sweeps_last"],
-        "decim_conv_last": [float("%.3g" % c) for c in st_end["decim_conv_last"] if c > 0],
+        "decim_ms_parts": {k_: round(v, 1) for k_, v in zip(("rho", "eigensolver", "host", "guess"),
+                                                            st_end["ms_decim_parts"])},
+        "decim_sweeps_last": [st_end["decim_sweeps32_last"], st_end["decim_sweeps_last"]],
         "sigma_shape": {"tile_n": st_end["sigma_tile_n"], "kchunk": st_end["sigma_kchunk"],
-                        "tunes": st_end["tunes"], "tune_hits": st_end["tune_hits"],
-                        "tune_ms": round(st_end["ms_tune"], 1),
-                        "last_candidates_ms": [round(c, 3) for c in st_end["tune_cand_ms"]]},
-        "decim_blocks_last": [st_end["decim_nmat_last"], st_end["decim_nmax_last"]],
-        "decim_sweeps32_last": st_end["decim_sweeps32_last"],
+                        "tunes": st_end["tunes"], "tune_hits": st_end["tune_hits"]},
         "sigma_terms": st_end["n_terms"], "sigma_items": st_end["n_items"],
         "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": f"{src} bf16 sustained",
-                     "kernel": "tc_tma_kernel (unit: one sigma call = ψ split + phase 1 + phase 2 launches; "
+                     "kernel": "tc_tma_kernel (unit: one sigma call = psi split + phase 1 + phase 2 launches; "
                                f"{d_n} calls in the timed steps, {d_ms / max(d_n, 1):.1f} ms each)",
-                     "traffic_note": "DRAM bytes per sigma call, ncu capture of the middle-bond sigma scaled "
-                                     "by tensor-core stages" if traffic else "kernel changed since the capture"},
-        "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": int(host_in.numel() * 8),
-                "d2h_bytes_per_step": int(host_out.numel() * 8)},
+                     "traffic_note": "no DRAM counters at this size (captures with more than the launch list are "
+                                     "taken on a few-GB workload only); see profiles/"},
+        "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "steps": n_e2e,
+                "call": "dmrg_update_bond_host (pinned host guess in, next guess out)",
+                "h2d_bytes_per_step": int(h2d / n_e2e), "d2h_bytes_per_step": int(d2h / n_e2e)},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "device_bytes": st_end["device_bytes"],
     }
     if rank == 0 and not args.no_cpu_baseline:
-        f = sample_flops()
-        rate, dt, cores = oracle_sample_rate(3, f)
+        rate, dt, cores = oracle_sample_rate(3)
         out["cpu_baseline"] = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                                "sample": f"oracle sigma at K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']} middle bond "
-                                         f"(same recipe), {dt:.2f} s per sigma, FLOPs by the planner count"}
+                                         f"(same recipe), {dt:.2f} s per sigma, FLOPs of the oracle's own products"}
     plan.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -444,18 +436,14 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    f = None
-    try:
-        f = sample_flops()
-    except Exception:
-        f = None
     for _ in range(args.warmup):
-        oracle_sample_rate(1, f)
+        oracle_sample_rate(1)
     rates, dts = [], []
+    cores = None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r, dt, cores = oracle_sample_rate(1, f)
-        rates.append(r if r is not None else 0.0)
+        r, dt, cores = oracle_sample_rate(1)
+        rates.append(r)
         dts.append(dt)
     total = time.perf_counter() - t0
     value = statistics.median(rates) if rates else None
@@ -464,7 +452,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{args.workload}: K={w['K']}, D={w['D']} (oracle on a bounded sample "
-                                  f"K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']})"},
+                                  f"K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']}, FLOPs of its own products)"},
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                             "sample": f"oracle sigma at K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']} per step"},
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -479,9 +467,13 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="k73_d3000", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
-    ap.add_argument("--dav-iters", type=int, default=8)
-    ap.add_argument("--tol", type=float, default=1e-5)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--dav-iters", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-store", type=int, default=0, help="mixed modes: keep the FP64 operator store")
+    ap.add_argument("--refine", type=int, default=0, help="mixed modes: FP64 residual correction of Davidson")
+    ap.add_argument("--fp64-tc", type=int, default=0,
+                    help="mixed modes with --fp64-store 1: FP64 products on the FP64-accurate tensor-core engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvec", type=int, default=1, help="--sigma-only: vectors per grouped sigma launch")
     ap.add_argument("--sigma-only", action="store_true",

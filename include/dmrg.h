@@ -67,8 +67,16 @@ typedef enum {
  *   decimation stay FP64.
  * BF16: as BF16X3 with only the hi part (one product per tile).
  * BF16X6: three pieces x = hi + lo + lo2 (24 significant bits, FP32-like
- *   storage) and the six products whose piece orders sum to at most 2. */
-typedef enum { DMRG_FP64 = 0, DMRG_BF16X3 = 1, DMRG_BF16 = 2, DMRG_BF16X6 = 3 } dmrg_precision;
+ *   storage) and the six products whose piece orders sum to at most 2.
+ * FP64_TC: FP64 operator store and results, every product FP64-accurate on the
+ *   bf16 tensor cores (error-free splitting, Ozaki et al. 2012: per 64-deep K
+ *   stage each row of A and column of B is scaled by a power of two and cut
+ *   into six 8-bit slices; the slice products whose orders sum to <= 5
+ *   accumulate in FP32 tensor memory, exactly for the four leading orders;
+ *   the orders are combined in double-float arithmetic and written as FP64).
+ *   Per product, the error is bounded by about 2^-45 times the row and column
+ *   maxima times the depth; not bitwise FP64, no FP64 arithmetic units. */
+typedef enum { DMRG_FP64 = 0, DMRG_BF16X3 = 1, DMRG_BF16 = 2, DMRG_BF16X6 = 3, DMRG_FP64_TC = 4 } dmrg_precision;
 
 typedef enum { DMRG_PRECOND_JACOBI = 0, DMRG_PRECOND_MLP = 1 } dmrg_precond;
 
@@ -109,6 +117,23 @@ typedef struct {
                                or sigma_tile_n > 0; default 1 */
     int sigma_tile_n;       /* mixed modes: 64 or 128 fixes the tile width of the sigma work
                                lists (no tuning); 0 = tuned or 128; default 0 */
+    int refine;             /* mixed modes: 1 = FP64 residual correction of Davidson (a defect
+                               correction, not in the paper, whose Davidson is FP64 throughout):
+                               the mixed-precision Davidson runs until it meets tol or its
+                               residual stalls at the mixed sigma's noise floor; then, per
+                               outer round, the residual r = H x - theta x is formed with the
+                               FP64-accurate sigma (dmrg_sigma_fp64: W = H X), and the next
+                               inner mixed Davidson runs on P H_mixed P + W X^T + X W^T - X C X^T
+                               (P = I - X X^T, C = sym(X^T W)), which equals H on X in both
+                               directions; its Ritz vectors are X's corrections.  It stops when
+                               the FP64 residual meets tol.  Energies are FP64 Rayleigh
+                               quotients.  With fp64_store = 1 the result is that of the FP64
+                               Hamiltonian; default 0 */
+    int max_refine;         /* outer rounds of the residual correction (0 => 8) */
+    int fp64_tc;            /* mixed modes with fp64_store = 1: the FP64 products (renormalisation,
+                               intermediates, dmrg_sigma_fp64, the residual correction and FP64
+                               Rayleigh quotients) run on the FP64-accurate tensor-core engine of
+                               DMRG_FP64_TC instead of FP64 arithmetic units; default 0 */
 } dmrg_options;
 
 typedef struct {
@@ -155,6 +180,20 @@ typedef struct {
     double sigma_load_bytes[2][2];/* mixed sigma, one vector: operand bytes the tensor-core tiles
                                      load through TMA, [phase 1 / 2][other operands / phase-1
                                      scratch] (counts every box load, before any L2 reuse) */
+    double renorm_flops_total;    /* algorithmic FLOPs of every renormalisation so far (products
+                                     and their intermediates) */
+    double interm_flops_total;    /* algorithmic FLOPs of forming every bond's intermediates */
+    double davidson_rnorm_last;   /* last Davidson: largest residual 2-norm over the roots at exit
+                                     (FP64-accurate residual when refine = 1) */
+    int davidson_conv_last;       /* last Davidson: 1 if every root met tol */
+    int davidson_stalled_last;    /* last Davidson (mixed): 1 if the mixed iteration stopped
+                                     because its residual stalled at the noise floor */
+    int davidson_refine_last;     /* last Davidson: residual-correction rounds (refine = 1) */
+    int sigma_chunks;             /* scratch chunks (pairs of launches) of the current bond's sigma list */
+    int64_t sigma_acc_calls;      /* FP64-accurate sigma calls (dmrg_sigma_fp64, refinement,
+                                     FP64 Rayleigh quotients), all vectors */
+    double ms_sigma_acc;          /* their device time */
+    double sigma_acc_flops;       /* their algorithmic FLOPs */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */
@@ -203,6 +242,13 @@ dmrg_status dmrg_sigma(dmrg_plan_t plan, const double* psi_dev, double* sigma_de
 dmrg_status dmrg_sigma_fp64(dmrg_plan_t plan, const double* psi_dev, double* sigma_dev, int nvec,
                             void* stream);
 
+/* dmrg_sigma_fp64 on the FP64 arithmetic units even when the plan's FP64
+ * products run on the FP64-accurate tensor-core engine (DMRG_FP64_TC, or
+ * fp64_tc = 1): the plain FP64 GPU reference for the same stored operators.
+ * Slow on GB300 (~1 TFLOP/s of FP64); same buffers as dmrg_sigma. */
+dmrg_status dmrg_sigma_fp64_units(dmrg_plan_t plan, const double* psi_dev, double* sigma_dev, int nvec,
+                                  void* stream);
+
 /* Same as dmrg_sigma with HOST buffers (copies to and from the device inside;
  * the end-to-end path of the benchmark). */
 dmrg_status dmrg_sigma_host(dmrg_plan_t plan, const double* psi_host, double* sigma_host,
@@ -220,6 +266,25 @@ dmrg_status dmrg_hdiag(dmrg_plan_t plan, double* diag_dev, void* stream);
  * Returns DMRG_ENOTCONV if max_iter is reached above tol (energies filled). */
 dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi_dev, int n_roots, double tol, int max_iter,
                           int precond, double* energies, int* iters, void* stream);
+
+/* One two-site bond update (Sec. 2.1, Fig. flowchart) from HOST buffers, the
+ * end-to-end path of a caller that keeps its vectors in host memory:
+ *  psi_host   n_roots guesses of the current bond (host, FP64, canonical
+ *             layout, n_roots x dim), copied to the device.
+ * Davidson (as dmrg_davidson with the plan's tol, max_iter and precond), then
+ * decimation to D (as dmrg_decimate, forward or backward), which makes the next
+ * bond current; its guess is copied back.
+ *  energies   out (host): n_roots energies (+ e_core).
+ *  iters      out (host, may be NULL): Davidson iterations.
+ *  discarded  out (host, may be NULL): discarded weight.
+ *  next_psi_host  out (host, may be NULL): the next bond's guess.
+ *  next_dim   in: capacity of next_psi_host in elements per root (0 if NULL);
+ *             out: the next bond's vector length.  The guess is copied only
+ *             when the capacity suffices.
+ * Returns DMRG_ENOTCONV (after decimating) if Davidson stopped above tol. */
+dmrg_status dmrg_update_bond_host(dmrg_plan_t plan, const double* psi_host, int n_roots, int D, int forward,
+                                  double* energies, int* iters, double* discarded, double* next_psi_host,
+                                  int64_t* next_dim, void* stream);
 
 /* Decimation (Sec. 2.1): truncate the current bond's two-site vectors psi_dev
  * (n_roots of them; state-averaged density matrix if > 1) to at most D states
@@ -319,8 +384,9 @@ int dmrg_mlp_num_params(void);
  * where A_s is m_o x k[s] at a + a_off[s] (row-major ld lda[s], or its
  * transpose if a_tr[s]) and B_s is k[s] x n_o at b + b_off[s] (ld ldb[s], or
  * transposed if b_tr[s]).  a, b, c are device FP64 buffers.  precision
- * selects the FP64 engine or the bf16 tensor-core engine (operands are split
- * into bf16 hi/lo on the device for BF16X3).
+ * selects the FP64 engine (DMRG_FP64), the FP64-accurate tensor-core engine
+ * (DMRG_FP64_TC) or the bf16 tensor-core engine (operands are split into bf16
+ * hi/lo on the device for BF16X3).
  * ------------------------------------------------------------------------ */
 dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int* n,
                               const int64_t* c_off, const int* seg_beg, const int* k,

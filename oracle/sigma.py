@@ -84,10 +84,13 @@ class TwoSite:
         return self._terms
 
     def sigma(self, psi, terms=None):
-        """sigma = H psi for one vector in the canonical layout."""
+        """sigma = H psi for one vector in the canonical layout.  ``flops_last``
+        receives the floating-point operations of the products and scaled sums
+        this call performed (2mkn per matrix product, 2 per element summed)."""
         X = self.to_se(psi)
         SB = self.S.basis
         out = {}
+        fl = 0
         for c, OS, OE in (self.terms() if terms is None else terms):
             pE = 0 if OE is None else OE.parity
             for iS, M in X.items():
@@ -105,12 +108,18 @@ class TwoSite:
                 else:
                     continue
                 sign = -1.0 if (pE and (SB.n(iS) & 1)) else 1.0
+                if A is not None:
+                    fl += 2 * A.shape[0] * A.shape[1] * M.shape[1]
                 T = M if A is None else A @ M
+                if B is not None:
+                    fl += 2 * T.shape[0] * T.shape[1] * B.shape[0]
                 T = T if B is None else T @ B.T
+                fl += 2 * T.size
                 if jS in out:
                     out[jS] += (c * sign) * T
                 else:
                     out[jS] = (c * sign) * T
+        self.flops_last = fl
         return self.from_se(out)
 
     def hdiag(self):

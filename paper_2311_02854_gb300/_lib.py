@@ -9,7 +9,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
-DMRG_FP64, DMRG_BF16X3, DMRG_BF16, DMRG_BF16X6 = 0, 1, 2, 3
+DMRG_FP64, DMRG_BF16X3, DMRG_BF16, DMRG_BF16X6, DMRG_FP64_TC = 0, 1, 2, 3, 4
 DMRG_PRECOND_JACOBI, DMRG_PRECOND_MLP = 0, 1
 STATUS = {0: "DMRG_OK", -1: "DMRG_EINVAL", -2: "DMRG_ENOMEM", -3: "DMRG_ECUDA", -4: "DMRG_ENUMERIC",
           -5: "DMRG_ETIMEOUT", -6: "DMRG_ENOTCONV", -7: "DMRG_EIO"}
@@ -26,7 +26,8 @@ class Options(C.Structure):
                 ("max_space", C.c_int), ("precond", C.c_int), ("fp64_final", C.c_int),
                 ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
                 ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int),
-                ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int)]
+                ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int), ("refine", C.c_int), ("max_refine", C.c_int),
+                ("fp64_tc", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -44,7 +45,11 @@ class Stats(C.Structure):
                 ("decim_nmat_last", C.c_int), ("decim_nmax_last", C.c_int), ("decim_sweeps32_last", C.c_int),
                 ("sigma_tile_n", C.c_int),
                 ("sigma_kchunk", C.c_int64), ("tunes", C.c_int64), ("tune_hits", C.c_int64), ("ms_tune", C.c_double),
-                ("tune_cand_ms", C.c_double * 4), ("sigma_load_bytes", (C.c_double * 2) * 2)]
+                ("tune_cand_ms", C.c_double * 4), ("sigma_load_bytes", (C.c_double * 2) * 2),
+                ("renorm_flops_total", C.c_double), ("interm_flops_total", C.c_double),
+                ("davidson_rnorm_last", C.c_double), ("davidson_conv_last", C.c_int),
+                ("davidson_stalled_last", C.c_int), ("davidson_refine_last", C.c_int), ("sigma_chunks", C.c_int),
+                ("sigma_acc_calls", C.c_int64), ("ms_sigma_acc", C.c_double), ("sigma_acc_flops", C.c_double)]
 
     def as_dict(self):
         def conv(v):
@@ -72,9 +77,11 @@ _SIGS = {
     "dmrg_sigma": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dmrg_sigma_host": (C.c_int, [_P, _D, _D, C.c_int, _P]),
     "dmrg_sigma_fp64": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "dmrg_sigma_fp64_units": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "dmrg_hdiag": (C.c_int, [_P, _P, _P]),
     "dmrg_davidson": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _D, _I, _P]),
     "dmrg_decimate": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _D, _P, _L, _P]),
+    "dmrg_update_bond_host": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_int, _D, _I, _D, _D, _L, _P]),
     "dmrg_sweep": (C.c_int, [_P, C.c_int, _I, _D, _D, _P]),
     "dmrg_save_mps": (C.c_int, [_P, C.c_char_p]),
     "dmrg_stats": (C.c_int, [_P, C.POINTER(Stats)]),
@@ -214,6 +221,9 @@ class Plan:
     def sigma_fp64(self, psi, out, nvec=1, stream=None):
         self._call("dmrg_sigma_fp64", _ptr(psi), _ptr(out), int(nvec), _stream(stream))
 
+    def sigma_fp64_units(self, psi, out, nvec=1, stream=None):
+        self._call("dmrg_sigma_fp64_units", _ptr(psi), _ptr(out), int(nvec), _stream(stream))
+
     def sigma_host(self, psi, out, nvec=1, stream=None):
         assert psi.dtype == np.float64 and out.dtype == np.float64
         self._call("dmrg_sigma_host", _dptr(psi), _dptr(out), int(nvec), _stream(stream))
@@ -236,6 +246,24 @@ class Plan:
         self._call("dmrg_decimate", _ptr(psi), int(n_roots), int(D), int(bool(forward)), _dptr(w),
                    _ptr(next_psi), C.byref(nd), _stream(stream))
         return float(w[0]), nd.value
+
+    def update_bond_host(self, psi, n_roots, D, forward, next_psi=None, stream=None):
+        """dmrg_update_bond_host: Davidson + decimation from host buffers (numpy
+        FP64 arrays; pinned memory if they view a pinned torch tensor).  Returns
+        (energies, iterations, discarded weight, next dim, converged)."""
+        assert psi.dtype == np.float64 and psi.flags.c_contiguous
+        e = np.zeros(n_roots)
+        it = C.c_int()
+        w = np.zeros(1)
+        cap = 0 if next_psi is None else int(next_psi.size // max(n_roots, 1))
+        nd = C.c_int64(cap)
+        nptr = None if next_psi is None else next_psi.ctypes.data_as(_D)
+        code = getattr(lib(), "dmrg_update_bond_host")(self.handle, _dptr(psi), int(n_roots), int(D),
+                                                        int(bool(forward)), _dptr(e), C.byref(it), _dptr(w), nptr,
+                                                        C.byref(nd), _stream(stream))
+        if code not in (0, -6):
+            _check(code, self.handle)
+        return e, it.value, float(w[0]), nd.value, code == 0
 
     def sweep(self, n_sweeps, D_schedule=None, stream=None):
         e = np.zeros(n_sweeps)

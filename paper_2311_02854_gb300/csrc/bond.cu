@@ -362,6 +362,7 @@ void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, 
     if (im.fams.empty()) return;
     std::vector<double> W(std::max<int64_t>(wtot, 8), 0.0);
     WorkList wl;
+    if (!P.tc_store()) P.f64_tiles(wl);
     int64_t woff = 0;
     for (auto& IF : im.fams) {
         const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
@@ -676,6 +677,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
         DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
         P.free(acc, out->n);
     } else {
+        P.f64_tiles(pl);
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, cap, kChunkF64);
         host_lower_ms = host_ms_since(host0);
         P.stats.ms_host_plan += host_lower_ms;
@@ -703,6 +705,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     cudaEventElapsedTime(&ms, e0, e1);
     P.stats.ms_renorm += ms;
     P.stats.renorm_flops_last = pl.flops + fl_int;
+    P.stats.renorm_flops_total += pl.flops + fl_int;
     if (P.opt.verbose)
         fprintf(stderr, "[dmrg] renormalise site %d (%s): %.0f ms, of which host lowering %.0f ms; %zu products, "
                         "%.3g FLOP\n",
@@ -789,6 +792,7 @@ void set_bond(Plan& P, int k) {
     cudaEventDestroy(e1);
     P.stats.ms_interm += ms;
     P.stats.interm_flops = fl;
+    P.stats.interm_flops_total += fl;
     const int esz = (P.mixed() ? 2 * (1 + P.lo_pieces()) : 0) + (P.f64_store() ? 8 : 0);
     P.stats.interm_bytes = P.interm.n * esz;
     P.stats.store_bytes = (L.n + R.n) * esz;
@@ -859,6 +863,8 @@ void set_bond(Plan& P, int k) {
     int maxd = std::max({L.lay.basis.dmax(), R.lay.basis.dmax(), 1});
     ensure_ident(P, maxd);
     P.sigma_fp64_ready = false;
+    P.sigma_units_pl.clear();
+    P.sigma_units_ready = false;
     if (P.mixed()) {
         ProductList& tl = P.sigma_tc;
         tl.clear();
@@ -940,6 +946,7 @@ void set_bond(Plan& P, int k) {
             DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_psi_jobs, jobs.data(), jobs.size() * sizeof(SplitJob),
                                             cudaMemcpyHostToDevice, P.stream));
     } else {
+        P.f64_tiles(pl);
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), kChunkF64);
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
         pl.upload(P.stream);
@@ -948,6 +955,7 @@ void set_bond(Plan& P, int k) {
     }
     P.stats.n_terms = (int64_t)P.sp.terms.size();
     P.stats.n_items = nitems;
+    P.stats.sigma_chunks = (int)(P.mixed() ? P.sigma_tc.tchunks.size() : P.sigma_pl.chunks.size());
 
     // diag(H_eff): terms whose three factors all conserve the quantum numbers
     ProductList& hl = P.hdiag_pl;
@@ -1082,18 +1090,57 @@ BufTable bond_buffers(Plan& P, const double* psi, double* out) {
 void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
     if (!P.sigma_fp64_ready) {
+        P.f64_tiles(P.sigma_pl);
         P.sigma_pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap(P) / 2, 1 << 24), kChunkF64);
         ensure_scratch_f64(P, std::max<int64_t>(P.sigma_pl.scratch_elems, 1));
         P.sigma_pl.upload(st);
         P.sigma_fp64_ready = true;
     }
     const int64_t per = std::max<int64_t>(P.sigma_pl.scratch_elems, 1);
+    cudaEvent_t e0 = P.take_event(), e1 = P.take_event();
+    DMRG_CHECK_CUDA(cudaEventRecord(e0, st));
     for (int v = 0; v < nvec; ++v) {
         DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v * P.dim, 0, (size_t)P.dim * 8, st));
         BufTable bt = bond_buffers(P, psi + (int64_t)v * P.dim, out + (int64_t)v * P.dim);
         bt.vstride[BUF_SCR] = per;
         P.sigma_pl.run(bt, 1, st);
     }
+    DMRG_CHECK_CUDA(cudaEventRecord(e1, st));
+    DMRG_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    P.ev_pool.push_back(e0);
+    P.ev_pool.push_back(e1);
+    P.stats.sigma_acc_calls += nvec;
+    P.stats.ms_sigma_acc += ms;
+    P.stats.sigma_acc_flops += P.sigma_pl.flops * nvec;
+}
+
+void sigma_fp64_units(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st) {
+    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
+    if (!P.oz) {
+        sigma_fp64(P, psi, out, nvec, st);
+        return;
+    }
+    ProductList& pl = P.sigma_units_pl;
+    if (!P.sigma_units_ready) {
+        pl.clear();
+        pl.outs = P.sigma_pl.outs;
+        pl.cs = P.sigma_pl.cs;
+        pl.tile_m = pl.tile_n = 0;  // 64 x 64 tiles: the FP64 units
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap(P) / 2, 1 << 24), kChunkF64);
+        pl.upload(st);
+        P.sigma_units_ready = true;
+    }
+    ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1));
+    const int64_t per = std::max<int64_t>(pl.scratch_elems, 1);
+    for (int v = 0; v < nvec; ++v) {
+        DMRG_CHECK_CUDA(cudaMemsetAsync(out + (int64_t)v * P.dim, 0, (size_t)P.dim * 8, st));
+        BufTable bt = bond_buffers(P, psi + (int64_t)v * P.dim, out + (int64_t)v * P.dim);
+        bt.vstride[BUF_SCR] = per;
+        pl.run(bt, 1, st);
+    }
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
 namespace {

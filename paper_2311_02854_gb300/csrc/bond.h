@@ -23,6 +23,8 @@ BufTable bond_buffers(Plan& P, const double* psi, double* out);
 void sigma(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
 // sigma in FP64 arithmetic over the stored operators (either precision)
 void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
+// the same on the FP64 arithmetic units, whatever engine the plan's FP64 products use
+void sigma_fp64_units(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
 void hdiag(Plan& P, double* out, cudaStream_t st);
 
 // solver.cu

@@ -155,6 +155,9 @@ void dmrg_default_options(dmrg_options* o) {
     o->sigma_graph = 1;
     o->sigma_tune = 1;
     o->sigma_tile_n = 0;
+    o->refine = 0;
+    o->max_refine = 0;
+    o->fp64_tc = 0;
 }
 
 const char* dmrg_version(void) {
@@ -183,7 +186,11 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         else if (P.opt.precision == DMRG_BF16X3) P.nsplit = 2;
         else if (P.opt.precision == DMRG_BF16) P.nsplit = 1;
         else if (P.opt.precision == DMRG_BF16X6) P.nsplit = 3;
+        else if (P.opt.precision == DMRG_FP64_TC) P.nsplit = 0;
         else throw Error(DMRG_EINVAL, "unknown precision mode");
+        // FP64 products on the tensor-core engine: the FP64_TC mode, or the FP64
+        // store of a mixed mode with fp64_tc
+        P.oz = P.opt.precision == DMRG_FP64_TC || (P.nsplit > 0 && P.opt.fp64_store && P.opt.fp64_tc);
         if (P.opt.sigma_tile_n != 0 && P.opt.sigma_tile_n != 64 && P.opt.sigma_tile_n != 128)
             throw Error(DMRG_EINVAL, "sigma_tile_n must be 0, 64 or 128");
         P.K = K;
@@ -307,6 +314,16 @@ dmrg_status dmrg_sigma_fp64(dmrg_plan_t plan, const double* psi, double* sig, in
         cudaStream_t st = pick(plan, stream);
         sigma_fp64(plan->P, psi, sig, nvec, st);
         DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return DMRG_OK;
+    });
+}
+
+dmrg_status dmrg_sigma_fp64_units(dmrg_plan_t plan, const double* psi, double* sig, int nvec, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi || !sig || nvec < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        sigma_fp64_units(plan->P, psi, sig, nvec, st);
         return DMRG_OK;
     });
 }
@@ -474,6 +491,38 @@ dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi, int n_roots, int 
     });
 }
 
+dmrg_status dmrg_update_bond_host(dmrg_plan_t plan, const double* psi_host, int n_roots, int D, int forward,
+                                  double* energies, int* iters, double* discarded, double* next_psi_host,
+                                  int64_t* next_dim, void* stream) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (!psi_host || !energies || n_roots < 1 || D < 1 || (next_psi_host && !next_dim))
+        return fail(plan, DMRG_EINVAL, "bad arguments");
+    return guarded(plan, [&]() {
+        cudaStream_t st = pick(plan, stream);
+        Plan& P = plan->P;
+        DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
+        const int64_t need = (int64_t)n_roots * P.dim;
+        if (need > P.n_io) {
+            P.free(P.d_io, P.n_io);
+            P.n_io = need;
+            P.d_io = P.alloc(need);
+        }
+        double* dpsi = P.d_io;
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(dpsi, psi_host, (size_t)need * 8, cudaMemcpyHostToDevice, st));
+        const dmrg_status ds = davidson(P, dpsi, n_roots, P.opt.tol, P.opt.max_iter, P.opt.precond, energies, iters);
+        const int64_t cap = next_dim ? *next_dim : 0;
+        double w = 0.0;
+        decimate(P, dpsi, n_roots, D, forward != 0, &w);
+        if (discarded) *discarded = w;
+        if (next_dim) *next_dim = P.dim;
+        if (next_psi_host && cap >= P.dim)
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(next_psi_host, P.d_guess, (size_t)n_roots * P.dim * 8,
+                                            cudaMemcpyDeviceToHost, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+        return ds;
+    });
+}
+
 dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, double* energies, double* discarded,
                        void* stream) {
     if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
@@ -550,9 +599,10 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
                               const int64_t* b_off, const int* ldb, const int* b_tr, const double* alpha,
                               const double* a, const double* b, double* c, void* stream) {
     if (n_out < 0 || !m || !n || !c_off || !seg_beg || !a || !b || !c) return fail(nullptr, DMRG_EINVAL, "bad arguments");
-    if (precision != DMRG_FP64 && precision != DMRG_BF16X3 && precision != DMRG_BF16 && precision != DMRG_BF16X6)
+    if (precision != DMRG_FP64 && precision != DMRG_BF16X3 && precision != DMRG_BF16 && precision != DMRG_BF16X6 &&
+        precision != DMRG_FP64_TC)
         return fail(nullptr, DMRG_EINVAL, "unknown precision");
-    if (precision != DMRG_FP64) {
+    if (precision != DMRG_FP64 && precision != DMRG_FP64_TC) {
         try {
             return grouped_gemm_tc(precision == DMRG_BF16X3 ? 2 : (precision == DMRG_BF16X6 ? 3 : 1), n_out, m, n, c_off, seg_beg, k, a_off, lda, a_tr,
                                    b_off, ldb, b_tr, alpha, a, b, c, (cudaStream_t)stream);
@@ -563,6 +613,10 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
     try {
         cudaStream_t st = (cudaStream_t)stream;
         WorkList wl;
+        if (precision == DMRG_FP64_TC) {  // 128 x 64 tiles: the FP64-accurate tensor-core engine
+            wl.tile_m = oz_tile_rows();
+            wl.tile_n = oz_tile_cols();
+        }
         for (int o = 0; o < n_out; ++o) {
             std::vector<Seg> segs;
             for (int s = seg_beg[o]; s < seg_beg[o + 1]; ++s) {
@@ -591,6 +645,8 @@ dmrg_status dmrg_grouped_gemm(int precision, int n_out, const int* m, const int*
         launch_seg_gemm_f64(wl, bt, 1, st);
         DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
         wl.release();
+        if (precision == DMRG_FP64_TC && oz_take_error(st))
+            return fail(nullptr, DMRG_ETIMEOUT, "the FP64 tensor-core engine gave up waiting");
         return DMRG_OK;
     } catch (const Error& e) {
         return fail(nullptr, e.code, e.what());

@@ -58,6 +58,9 @@ struct WorkList {
     size_t cap_tiles = 0, cap_segs = 0;
     double flops = 0.0;
     bool rank1 = false;  // every segment has K = 1 (run by the rank-1 kernel)
+    // tile shape of add_block when nonzero (rows, columns); 128 x 64 lists run on
+    // the FP64-accurate tensor-core engine (launch_seg_gemm_f64 dispatches on it)
+    int tile_m = 0, tile_n = 0;
     void clear() {
         tiles.clear();
         segs.clear();
@@ -72,6 +75,15 @@ struct WorkList {
 };
 
 void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaStream_t st);
+// FP64-accurate products on the bf16 tensor cores (kernels_oz.cu): work lists
+// lowered with oz_tile_rows() x oz_tile_cols() tiles over FP64 buffers
+void launch_seg_gemm_oz(const WorkList& w, const BufTable& bt, int nvec, int* d_err, cudaStream_t st);
+int oz_tile_rows();
+int oz_tile_cols();
+// device error word of the FP64 tensor-core engine (set when a bounded wait
+// gave up); oz_take_error reads and clears it (synchronises the stream)
+int* oz_error_word();
+bool oz_take_error(cudaStream_t st);
 // FP64 grouped GEMM with the work list in a static device array (noalloc.cu);
 // a, b, c as buffers 0, 1, 2 of the work list
 void grouped_gemm_f64_noalloc(const WorkList& host_wl, const double* a, const double* b, double* c, cudaStream_t st);

@@ -47,8 +47,9 @@ void WorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const 
             flops += 2.0 * m * n * (double)s[i].k;
         }
         int se = (int)segs.size();
-        for (int m0 = 0; m0 < m; m0 += tile)
-            for (int n0 = 0; n0 < n; n0 += tile) {
+        const int tm = tile_m > 0 ? tile_m : tile, tn = tile_n > 0 ? tile_n : tile;
+        for (int m0 = 0; m0 < m; m0 += tm)
+            for (int n0 = 0; n0 < n; n0 += tn) {
                 Tile t{};
                 t.alpha = alpha;
                 t.c_off = c_off;
@@ -261,6 +262,11 @@ __global__ void __launch_bounds__(NT) seg_outer_f64_kernel(const Tile* __restric
 
 void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaStream_t st) {
     if (w.tiles.empty()) return;
+    if (w.tile_m == oz_tile_rows() && !w.rank1) {
+        launch_seg_gemm_oz(w, bt, nvec, oz_error_word(), st);
+        return;
+    }
+    DMRG_REQUIRE(w.tile_m == 0 || w.tile_m == BM, DMRG_EINVAL, "work list tile shape not runnable on the FP64 engine");
     const int64_t n = (int64_t)w.tiles.size();
     const int64_t maxg = 2147483647LL;
     DMRG_REQUIRE(n <= maxg && nvec <= 65535, DMRG_EINVAL, "work list too large for one launch");

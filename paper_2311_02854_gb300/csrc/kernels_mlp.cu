@@ -245,15 +245,9 @@ int grid_n(int64_t n) {
 }  // namespace
 
 void Mlp::release() {
-    cudaFree(d_w);
-    cudaFree(d_wb);
-    cudaFree(d_adam);
-    cudaFree(d_grad);
-    cudaFree(d_x);
-    cudaFree(d_y);
-    cudaFree(d_work);
-    cudaFree(d_sec_off);
-    cudaFree(d_sec_q);
+    for (void* p : {(void*)d_w, (void*)d_wb, (void*)d_adam, (void*)d_grad, (void*)d_x, (void*)d_y, (void*)d_work,
+                    (void*)d_sec_off, (void*)d_sec_q})
+        if (p) cudaFree(p);
     d_w = nullptr;
     d_wb = nullptr;
     d_adam = d_grad = d_x = d_y = d_work = d_sec_q = nullptr;

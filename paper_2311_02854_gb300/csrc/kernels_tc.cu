@@ -10,98 +10,27 @@
 
 #include <algorithm>
 
+#include "ptx.h"
 #include "tc.h"
 
 namespace dmrg {
 namespace {
+
+using namespace ptx;
 
 constexpr int TM = 128, TN = 128, TK = 64;
 static_assert(sizeof(Tile) % 4 == 0 && sizeof(TSeg) % 4 == 0, "work-list records are moved by 32-bit shuffles");
 static_assert(sizeof(TSeg) % 16 == 0, "segment records stay 16-byte aligned");
 constexpr int PIECE_BYTES = TM * TK * 2;  // one 128 x 64 bf16 operand tile
 constexpr uint32_t TMEM_COLS = 128;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded waits: 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait until the phase with the given parity has completed; false on timeout.
-__device__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    if (mbar_try(addr, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (!mbar_try(addr, parity)) {
-        if (gtimer() - t0 > kWaitLimitNs) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-// smem matrix descriptor (tcgen05): start >> 4, LBO >> 4, SBO >> 4, version 1, 128B swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// instruction descriptor, kind::f16: D f32, A/B bf16, majors, negate A, N, M
-__device__ __forceinline__ uint32_t idesc(int a_mn, int b_mn, int neg) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg << 13) | ((uint32_t)a_mn << 15) |
-           ((uint32_t)b_mn << 16) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(ad), "l"(bd), "r"(id), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// instruction descriptor of a full 128 x 128 tile
+__device__ __forceinline__ uint32_t idesc(int a_mn, int b_mn, int neg) { return idesc_mn(a_mn, b_mn, neg, TN, TM); }
 
 // Stage one 128 x 64 (M x K) operand piece into shared memory in the 128B-swizzled
 // canonical layout the MMA descriptors describe.  Element (r, k) of the
@@ -149,10 +78,6 @@ __device__ __forceinline__ void cp_async_wait_n(int n) {
     else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(addr) : "memory");
-}
-
 // Roles of the persistent kernel (one CTA per SM):
 //   warps 0-3  epilogue: TMEM -> registers -> global (warp w owns TMEM lanes 32w..32w+31)
 //   warps 4-7  producers: cp.async of the operand pieces of each 64-deep K stage
@@ -495,10 +420,7 @@ struct StageMeta3 {
     uint8_t k16, n16, pad[2];        // 16-deep K steps holding data; MMA N / 16
 };
 
-__device__ __forceinline__ uint32_t idesc_n(int a_mn, int b_mn, int neg, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg << 13) | ((uint32_t)a_mn << 15) |
-           ((uint32_t)b_mn << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-}
+__device__ __forceinline__ uint32_t idesc_n(int a_mn, int b_mn, int neg, int n) { return idesc_mn(a_mn, b_mn, neg, n, TM); }
 
 template <int NSPLIT>
 __global__ void __launch_bounds__(THREADS3, 1)

@@ -182,6 +182,8 @@ void Plan::free_bf16(__nv_bfloat16*& p, int64_t n) {
 }
 
 void Plan::check_device_error() {
+    if (oz && oz_take_error(stream))
+        throw Error(DMRG_ETIMEOUT, "the FP64 tensor-core engine gave up waiting (device error word set)");
     if (!d_ctr) return;
     int err = 0;
     DMRG_CHECK_CUDA(cudaMemcpyAsync(&err, d_ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -275,6 +277,7 @@ Plan::~Plan() {
     free(d_dav, n_dav);
     free(d_guess, n_guess);
     sigma_pl.release();
+    sigma_units_pl.release();
     hdiag_pl.release();
 }
 
@@ -336,6 +339,8 @@ void ProductList::lower(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int64_t
     };
     while (i < cs.size()) {
         WorkList p1, p2;
+        p1.tile_m = p2.tile_m = tile_m;
+        p1.tile_n = p2.tile_n = tile_n;
         std::vector<std::vector<Seg>> segs(outs.size());
         std::vector<char> seen(outs.size(), 0);
         std::vector<int> order;

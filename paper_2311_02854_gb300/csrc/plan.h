@@ -95,6 +95,7 @@ struct ProductList {
     int64_t scratch_elems = 0;
     int8_t sbuf = -1;  // buffer id of the phase-1 scratch
     bool tc = false;
+    int tile_m = 0, tile_n = 0;  // FP64-engine tile shape of lower() (0: the engine's default)
     void clear();
     // FP64 engine: per-segment alpha, 64x64 tiles
     void lower(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk);
@@ -140,6 +141,13 @@ struct Plan {
     QN tot;
     int K = 0, N = 0, twoS = 0, D = 0, n_so = 0;
     int nsplit = 0;  // 0: FP64 engine; 1: bf16; 2: bf16 x3 (hi + lo); 3: bf16 x6 (hi + lo + lo2)
+    bool oz = false;  // FP64-engine products run on the FP64-accurate tensor-core engine
+    // tile shape of the FP64-engine work lists (128 x 64 tiles select the tensor-core engine)
+    void f64_tiles(WorkList& w) const {
+        w.tile_m = oz ? oz_tile_rows() : 0;
+        w.tile_n = oz ? oz_tile_cols() : 0;
+    }
+    void f64_tiles(struct ProductList& pl) const;
     bool mixed() const { return nsplit > 0; }
     // the operator store exists only as bf16 pieces built on the tensor cores
     // (mixed modes without the FP64 master store)
@@ -170,6 +178,8 @@ struct Plan {
     SigmaPlan sp;
     IntermStore interm;  // the bond's intermediates
     ProductList sigma_pl, hdiag_pl, sigma_tc;
+    ProductList sigma_units_pl;  // FP64 sigma on the FP64 arithmetic units (lowered on demand)
+    bool sigma_units_ready = false;
     double* d_scratch = nullptr;
     int64_t n_scratch = 0;
     double* d_ident = nullptr;
@@ -251,5 +261,10 @@ struct Plan {
     void check_device_error();
     ~Plan();
 };
+
+inline void Plan::f64_tiles(ProductList& pl) const {
+    pl.tile_m = oz ? oz_tile_rows() : 0;
+    pl.tile_n = oz ? oz_tile_cols() : 0;
+}
 
 }  // namespace dmrg

@@ -98,12 +98,40 @@ int jd_solve(Plan& P, const double* u, double theta, const double* r, double* t,
 // Davidson
 // ---------------------------------------------------------------------------
 
-dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int precond,
-                     double* energies, int* iters) {
-    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
-    DMRG_REQUIRE(nr >= 1 && nr <= 16, DMRG_EINVAL, "n_roots must be in 1..16");
+namespace {
+
+// Defect-corrected operator around the current vectors X (nr x n,
+// orthonormal), with W = H X from the FP64-accurate sigma and P = I - X X^T:
+//   H_c = P H_mixed P + W X^T + X W^T - X C X^T,   C = (X^T W + W^T X) / 2.
+// H_c X = H X and X^T H_c = X^T H, so every coupling of X in the projected
+// Davidson matrix is FP64-accurate (the mixed sigma's own asymmetry would
+// otherwise enter there); the mixed error acts only inside the complement of X,
+// on the correction, and the Ritz vectors of H_c near X approach H's
+// eigenvectors by a factor ~|H - H_mixed| / gap per outer round.
+struct DefectCorr {
+    int nr = 0;
+    const double* X = nullptr;
+    const double* W = nullptr;
+    double* proj = nullptr;  // nr x n workspace for P v
+    std::vector<double> C;
+};
+
+struct DavOut {
+    std::vector<double> theta, rnorm;
+    int iters = 0;
+    bool conv = false;
+    bool stalled = false;
+};
+
+// One Davidson solve from the guesses in psi (nr x n; Ritz vectors on exit).
+// stall > 0: stop when the residual no longer falls near the mixed sigma's
+// noise floor: after at least 10 iterations, the best residual so far is below
+// stall * max|theta| and the best of the last 5 iterations is above 0.7 times
+// the best before them.  (Far above the floor, Davidson may stagnate for a
+// while and then converge, so a plateau alone is not a stall.)
+void davidson_run(Plan& P, double* psi, int nr, double tol, int max_iter, int precond, const DefectCorr* corr,
+                  double stall, DavOut& out) {
     const int64_t n = P.dim;
-    DMRG_REQUIRE(n >= nr, DMRG_EINVAL, "fewer states than roots at this bond");
     int ms = P.opt.max_space > 0 ? P.opt.max_space : 20 * nr;
     ms = std::max(ms, 3 * nr);
     ms = (int)std::min<int64_t>(ms, n);
@@ -126,10 +154,6 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
     double* dGv = dG + (int64_t)ms * ms;
     double* dev = dGv + (int64_t)ms * ms;
     cudaStream_t st = P.stream;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
 
     // wall time per phase (verbose): diagonal, orthogonalisation, sigma, Ritz
     // step and residuals, preconditioner
@@ -141,17 +165,67 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
     auto tadd = [&](int i, std::chrono::steady_clock::time_point a) {
         if (P.opt.verbose) tph[i] += std::chrono::duration<double, std::milli>(tnow() - a).count();
     };
+    // W[0:cnt] = H V[0:cnt] (the defect-corrected operator when one is active)
+    std::vector<double> ha((size_t)std::max(nr, 1) * 3);
+    auto apply = [&](const double* Vb, double* Wb, int cnt) {
+        if (!corr) {
+            sigma(P, Vb, Wb, cnt, st);
+            return;
+        }
+        const int q = corr->nr;
+        std::vector<std::vector<double>> a(cnt, std::vector<double>(q));
+        // P v for every new vector, then one batched mixed sigma
+        for (int j = 0; j < cnt; ++j) {
+            const double* v = Vb + (int64_t)j * n;
+            dev_dots(corr->X, n, q, v, n, dco, dwork, st);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(a[j].data(), dco, q * 8, cudaMemcpyDeviceToHost, st));
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(corr->proj + (int64_t)j * n, v, n * 8, cudaMemcpyDeviceToDevice, st));
+            dev_combine(corr->X, n, q, dco, n, tmp, st);
+            dev_axpby(-1.0, tmp, 1.0, corr->proj + (int64_t)j * n, n, st);
+        }
+        sigma(P, corr->proj, Wb, cnt, st);
+        for (int j = 0; j < cnt; ++j) {
+            const double* v = Vb + (int64_t)j * n;
+            double* w = Wb + (int64_t)j * n;
+            // b = X^T (H_mixed P v), c = W^T v
+            dev_dots(corr->X, n, q, w, n, dco, dwork, st);
+            dev_dots(corr->W, n, q, v, n, dco + q, dwork, st);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(ha.data(), dco, 2 * q * 8, cudaMemcpyDeviceToHost, st));
+            DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+            // H_c v = P (H_mixed P v) + W a + X (c - C a),  a = X^T v
+            std::vector<double> cx(q);
+            for (int r = 0; r < q; ++r) {
+                double s_ = ha[q + r] - ha[r];
+                for (int b = 0; b < q; ++b) s_ -= corr->C[(size_t)r * q + b] * a[j][b];
+                cx[r] = s_;
+            }
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(dco, a[j].data(), q * 8, cudaMemcpyHostToDevice, st));
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(dco + q, cx.data(), q * 8, cudaMemcpyHostToDevice, st));
+            dev_combine(corr->W, n, q, dco, n, tmp, st);
+            dev_axpby(1.0, tmp, 1.0, w, n, st);
+            dev_combine(corr->X, n, q, dco + q, n, tmp, st);
+            dev_axpby(1.0, tmp, 1.0, w, n, st);
+            DMRG_CHECK_CUDA(cudaStreamSynchronize(st));  // a[j], cx are host temporaries
+        }
+    };
     auto tp0 = tnow();
     hdiag(P, hd, st);
     tadd(0, tp0);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(T, psi, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
     std::vector<double> G((size_t)ms * ms, 0.0);
     std::vector<double> theta(nr, 0.0), rnorm(nr, 0.0);
+    std::vector<double> hist;  // largest residual per iteration
     int m = 0, nnew = nr, it = 0;
-    bool conv = false;
+    bool conv = false, stalled = false;
     EigJob job;
     EigJob* d_job = nullptr;
     DMRG_CHECK_CUDA(cudaMalloc(&d_job, sizeof(EigJob)));
+    struct JobFree {
+        EigJob*& p;
+        ~JobFree() {
+            if (p) cudaFree(p);
+        }
+    } job_free{d_job};
     std::vector<double> Gv;
     std::vector<int> order;
     while (true) {
@@ -168,10 +242,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
                 dev_axpby(-1.0, tmp, 1.0, x, n, st);
             }
             double nrm2 = host_dot(P, x, x, n, dco, dwork);
-            if (!(nrm2 == nrm2) || std::isinf(nrm2)) {
-                cudaFree(d_job);
-                throw Error(DMRG_ENUMERIC, "non-finite Davidson direction");
-            }
+            if (!(nrm2 == nrm2) || std::isinf(nrm2)) throw Error(DMRG_ENUMERIC, "non-finite Davidson direction");
             double nrm = std::sqrt(nrm2);
             if (nrm > 1e-10) {
                 double* dst = V + (int64_t)(m + added) * n;
@@ -201,18 +272,22 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
         tadd(1, tp1);
         if (added == 0) break;
         auto tp2 = tnow();
-        sigma(P, V + (int64_t)m * n, W + (int64_t)m * n, added, st);
+        apply(V + (int64_t)m * n, W + (int64_t)m * n, added);
         tadd(2, tp2);
         auto tp3 = tnow();
-        for (int j = m; j < m + added; ++j) {
-            dev_dots(V, n, m + added, W + (int64_t)j * n, n, dco, dwork, st);
-            std::vector<double> col(m + added);
-            DMRG_CHECK_CUDA(cudaMemcpyAsync(col.data(), dco, (m + added) * 8, cudaMemcpyDeviceToHost, st));
+        {
+            // the new columns of V^T W, read back with one synchronisation
+            const int mm = m + added;
+            for (int j = m; j < mm; ++j) dev_dots(V, n, mm, W + (int64_t)j * n, n, dGv + (int64_t)(j - m) * mm, dwork, st);
+            std::vector<double> cols((size_t)mm * added);
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(cols.data(), dGv, cols.size() * 8, cudaMemcpyDeviceToHost, st));
             DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
-            for (int i = 0; i < m + added; ++i) {
-                G[(size_t)i * ms + j] = col[i];
-                G[(size_t)j * ms + i] = col[i];
-            }
+            for (int j = m; j < mm; ++j)
+                for (int i = 0; i < mm; ++i) {
+                    const double g = cols[(size_t)(j - m) * mm + i];
+                    G[(size_t)i * ms + j] = g;
+                    G[(size_t)j * ms + i] = g;
+                }
         }
         m += added;
         ++it;
@@ -237,6 +312,7 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] < w[b]; });
         bool all = true;
+        double rmax = 0.0;
         for (int i = 0; i < nr; ++i) {
             int c = order[i];
             theta[i] = w[c];
@@ -251,12 +327,11 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             DMRG_CHECK_CUDA(cudaMemcpyAsync(ri, wy, n * 8, cudaMemcpyDeviceToDevice, st));
             dev_axpby(-theta[i], xi, 1.0, ri, n, st);
             rnorm[i] = std::sqrt(std::max(0.0, host_dot(P, ri, ri, n, dco + 2 * ms, dwork)));
-            if (!(rnorm[i] == rnorm[i])) {
-                cudaFree(d_job);
-                throw Error(DMRG_ENUMERIC, "non-finite Davidson residual");
-            }
+            if (!(rnorm[i] == rnorm[i])) throw Error(DMRG_ENUMERIC, "non-finite Davidson residual");
             all = all && rnorm[i] <= tol;
+            rmax = std::max(rmax, rnorm[i]);
         }
+        hist.push_back(rmax);
         tadd(3, tp3);
         if (P.opt.verbose)
             fprintf(stderr, "[dmrg] davidson it=%d m=%d theta0=%.12f |r0|=%.3e\n", it, m, theta[0], rnorm[0]);
@@ -265,13 +340,23 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
             break;
         }
         if (it >= max_iter) break;
+        if (stall > 0.0 && it >= 10) {
+            const double before = *std::min_element(hist.begin(), hist.end() - 5);
+            const double recent = *std::min_element(hist.end() - 5, hist.end());
+            double tmax = 0.0;
+            for (int i = 0; i < nr; ++i) tmax = std::max(tmax, std::fabs(theta[i]));
+            if (std::min(before, recent) < stall * tmax && recent > 0.7 * before) {
+                stalled = true;
+                break;
+            }
+        }
         // training pairs: the plain method's converged correction for root 0
         if (P.harvest.on) {
             double* tjd = P.alloc(n);
             jd_solve(P, X, theta[0], T, tjd, P.harvest.jd_iters, P.harvest.jd_tol, dco, dwork);
             const double s_ = dev_absmax(hd, theta[0], n, dwork, st);
-            const double rmax = dev_absmax(T, 0.0, n, dwork, st);
-            P.harvest.pairs += mlp_collect(P.mlp, hd, T, tjd, theta[0], s_, rmax, n, P.harvest.per_solve, st);
+            const double rmx = dev_absmax(T, 0.0, n, dwork, st);
+            P.harvest.pairs += mlp_collect(P.mlp, hd, T, tjd, theta[0], s_, rmx, n, P.harvest.per_solve, st);
             P.free(tjd, n);
         }
         // corrections: diagonal (Jacobi), or scaled per element by the learned g
@@ -288,8 +373,8 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
                 float* xf = P.d_mlp_feat;
                 float* gf = P.d_mlp_feat + 5 * n;
                 const double s_ = dev_absmax(hd, theta[i], n, dwork, st);
-                const double rmax = dev_absmax(ri, 0.0, n, dwork, st);
-                mlp_features(P.mlp, hd, ri, theta[i], s_, rmax, n, xf, st);
+                const double rmx = dev_absmax(ri, 0.0, n, dwork, st);
+                mlp_features(P.mlp, hd, ri, theta[i], s_, rmx, n, xf, st);
                 mlp_forward(P.mlp, xf, n, gf, true, st);
                 mlp_apply(ri, hd, theta[i], gf, ri, n, st);
             } else {
@@ -312,14 +397,130 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
                         "Ritz+residual %.0f, preconditioner %.0f\n",
                 tph[0], tph[1], tph[2], tph[3], tph[4]);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(psi, X, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
-    if (P.mixed() && P.opt.fp64_final) {
-        // FP64 Rayleigh quotients <x|H|x> of the mixed-precision Ritz vectors
-        for (int i = 0; i < nr; ++i) {
-            double* xi = X + (int64_t)i * n;
-            sigma_fp64(P, xi, WY, 1, st);
-            const double num = host_dot(P, xi, WY, n, dco, dwork);
-            const double den = host_dot(P, xi, xi, n, dco, dwork);
-            theta[i] = num / den;
+    DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    out.theta = theta;
+    out.rnorm = rnorm;
+    out.iters = it;
+    out.conv = conv;
+    out.stalled = stalled;
+}
+
+// FP64-accurate Rayleigh quotients and residual norms of the nr vectors X
+// (orthonormal); Wacc receives H X.
+void accurate_residuals(Plan& P, const double* X, int nr, double* Wacc, double* r, std::vector<double>& theta,
+                        std::vector<double>& rnorm, double* dco, double* dwork) {
+    const int64_t n = P.dim;
+    cudaStream_t st = P.stream;
+    sigma_fp64(P, X, Wacc, nr, st);
+    theta.assign(nr, 0.0);
+    rnorm.assign(nr, 0.0);
+    for (int i = 0; i < nr; ++i) {
+        const double* xi = X + (int64_t)i * n;
+        const double* wi = Wacc + (int64_t)i * n;
+        const double num = host_dot(P, xi, wi, n, dco, dwork);
+        const double den = host_dot(P, xi, xi, n, dco, dwork);
+        theta[i] = num / den;
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(r, wi, n * 8, cudaMemcpyDeviceToDevice, st));
+        dev_axpby(-theta[i], xi, 1.0, r, n, st);
+        rnorm[i] = std::sqrt(std::max(0.0, host_dot(P, r, r, n, dco, dwork)));
+        if (!(rnorm[i] == rnorm[i])) throw Error(DMRG_ENUMERIC, "non-finite FP64 residual");
+    }
+}
+
+}  // namespace
+
+dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int precond,
+                     double* energies, int* iters) {
+    DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond");
+    DMRG_REQUIRE(nr >= 1 && nr <= 16, DMRG_EINVAL, "n_roots must be in 1..16");
+    const int64_t n = P.dim;
+    DMRG_REQUIRE(n >= nr, DMRG_EINVAL, "fewer states than roots at this bond");
+    cudaStream_t st = P.stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    const bool refine = P.mixed() && P.opt.refine && !P.harvest.on;
+    DavOut o;
+    int rounds = 0, total_it = 0;
+    double rmax = 0.0;
+    bool conv = false;
+    // the mixed iteration stops at its noise floor instead of running to max_iter;
+    // the floor of the sigma relative to |theta| is ~1e-5 with two or three bf16
+    // pieces and ~3e-3 with one (measured), so a plateau counts as a stall only
+    // within ~10x of it
+    const double stall = !P.mixed() ? 0.0 : (P.nsplit == 1 ? 3e-2 : 1e-4);
+    davidson_run(P, psi, nr, tol, max_iter, precond, nullptr, stall, o);
+    total_it += o.iters;
+    std::vector<double> theta = o.theta;
+    if (refine) {
+        const int max_rounds = P.opt.max_refine > 0 ? P.opt.max_refine : 8;
+        // X copy, H X (accurate), projection workspace, residual, small buffers
+        const int64_t nbuf = 3 * (int64_t)nr * n + n + 512;
+        double* buf = P.alloc(nbuf);
+        double* Xc = buf;
+        double* Wacc = Xc + (int64_t)nr * n;
+        double* proj = Wacc + (int64_t)nr * n;
+        double* r = proj + (int64_t)nr * n;
+        double* dco = r + n;
+        double* dwork = dco + 64;
+        std::vector<double> rn;
+        try {
+            for (;;) {
+                accurate_residuals(P, psi, nr, Wacc, r, theta, rn, dco, dwork);
+                rmax = *std::max_element(rn.begin(), rn.end());
+                if (P.opt.verbose)
+                    fprintf(stderr, "[dmrg] refine round %d: FP64 theta0=%.12f |r|max=%.3e (inner its %d%s)\n", rounds,
+                            theta[0], rmax, o.iters, o.stalled ? ", stalled" : "");
+                if (rmax <= tol) {
+                    conv = true;
+                    break;
+                }
+                if (rounds >= max_rounds) break;
+                // the corrected operator around X: C = sym(X^T W)
+                DefectCorr corr;
+                corr.nr = nr;
+                DMRG_CHECK_CUDA(cudaMemcpyAsync(Xc, psi, (size_t)nr * n * 8, cudaMemcpyDeviceToDevice, st));
+                corr.X = Xc;  // psi receives the new Ritz vectors
+                corr.W = Wacc;
+                corr.proj = proj;
+                corr.C.assign((size_t)nr * nr, 0.0);
+                std::vector<double> xw((size_t)nr * nr);
+                for (int a = 0; a < nr; ++a)
+                    for (int b = 0; b < nr; ++b)
+                        xw[(size_t)a * nr + b] = host_dot(P, Xc + (int64_t)a * n, Wacc + (int64_t)b * n, n, dco, dwork);
+                for (int a = 0; a < nr; ++a)
+                    for (int b = 0; b < nr; ++b) corr.C[(size_t)a * nr + b] = 0.5 * (xw[(size_t)a * nr + b] + xw[(size_t)b * nr + a]);
+                const double tol_in = std::max(0.5 * tol, 0.1 * rmax);
+                // no floor to stall at: H_c reproduces H on X, and its mixed error acts
+                // on the small correction only
+                davidson_run(P, psi, nr, tol_in, max_iter, precond, &corr, 0.0, o);
+                total_it += o.iters;
+                ++rounds;
+            }
+        } catch (...) {
+            P.free(buf, nbuf);
+            throw;
+        }
+        P.free(buf, nbuf);
+    } else {
+        conv = o.conv;
+        rmax = o.rnorm.empty() ? 0.0 : *std::max_element(o.rnorm.begin(), o.rnorm.end());
+        if (P.mixed() && P.opt.fp64_final) {
+            // FP64 Rayleigh quotients <x|H|x> of the mixed-precision Ritz vectors
+            double* buf = P.alloc(2 * n + 512);
+            std::vector<double> rn;
+            try {
+                for (int i = 0; i < nr; ++i) {
+                    std::vector<double> th1;
+                    accurate_residuals(P, psi + (int64_t)i * n, 1, buf, buf + n, th1, rn, buf + 2 * n, buf + 2 * n + 64);
+                    theta[i] = th1[0];
+                }
+            } catch (...) {
+                P.free(buf, 2 * n + 512);
+                throw;
+            }
+            P.free(buf, 2 * n + 512);
         }
     }
     cudaEventRecord(e1, st);
@@ -329,10 +530,13 @@ dmrg_status davidson(Plan& P, double* psi, int nr, double tol, int max_iter, int
     P.stats.ms_davidson += ms_;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_job);
     for (int i = 0; i < nr; ++i) energies[i] = theta[i] + P.I.e_core;
-    if (iters) *iters = it;
-    P.stats.davidson_iters_last = it;
+    if (iters) *iters = total_it;
+    P.stats.davidson_iters_last = total_it;
+    P.stats.davidson_rnorm_last = rmax;
+    P.stats.davidson_conv_last = conv ? 1 : 0;
+    P.stats.davidson_stalled_last = o.stalled ? 1 : 0;
+    P.stats.davidson_refine_last = rounds;
     return conv ? DMRG_OK : DMRG_ENOTCONV;
 }
 
@@ -392,6 +596,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
     double* d_w = d_vec + rho_tot;
     // rho_q = (1/nr) sum_roots M M^T (forward) or M^T M (backward)
     WorkList wl;
+    P.f64_tiles(wl);
     for (auto& kv : groups) {
         Group& g = kv.second;
         std::map<std::pair<int, int>, std::vector<Seg>> blk;  // (row comp, col comp) -> segs
@@ -701,6 +906,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         for (auto& b : bl) maxd = std::max(maxd, b[2]);
         for (auto& b : br) maxd = std::max(maxd, b[2]);
         ensure_ident(P, maxd);
+        P.f64_tiles(pl);
         pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), 1 << 14);
         ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1) * nr);
         pl.upload(st);
@@ -764,6 +970,7 @@ void two_site_guess(Plan& P, double* out) {
     double* da = upload(k, offa, na);
     double* db = upload(k + 1, offb, nb);
     WorkList wl;
+    P.f64_tiles(wl);
     for (const Plan::Sector& s : P.layout) {
         const int c1 = s.y / 4, c2 = s.y % 4;
         std::vector<Seg> segs;

@@ -1,13 +1,19 @@
 """Mixed-precision path (tcgen05 on bf16 pieces) against the FP64 oracle.
 
-The mixed-mode targets (sigma relative error <= 1e-5, energies within 1e-6 Eh)
-are held by BF16X3 sigma over an FP64 operator store (fp64_store = 1) with the
-FP64 Rayleigh quotient (fp64_final = 1).  When the operator store itself is
-built on the tensor cores, the FP32 accumulation in tensor memory (about 2^-23
-per 16-deep MMA step, inherited by every later bond) bounds the store at a few
-1e-6 relative; those modes are held to their measured bounds: sigma <= 1e-5
-(small) and 2e-5 (multi-tile), energies <= 1e-4 Eh (BF16X3) and 5e-5 Eh
-(BF16X6).  Plain BF16 is held to relative error <= 3e-2."""
+Which modes meet the mixed-path targets (sigma relative error <= 1e-5,
+energies within 1e-6 Eh), as these tests measure them:
+* BF16X3 sigma over an FP64 operator store (fp64_store = 1) meets the sigma
+  target; with the FP64 Rayleigh quotient (fp64_final = 1) or the FP64
+  residual correction (refine = 1, tests/test_gpu_paths.py) it meets the
+  energy target.
+* BF16X3 and BF16X6 with the operator store built on the tensor cores do NOT
+  meet them: the FP32 accumulation in tensor memory (about 2^-23 per 16-deep
+  MMA step, inherited by every later bond) leaves the store at a few 1e-6
+  relative, and sigma at 1.1e-5 (K=14, BF16X3).  These tests hold those modes
+  to their measured values -- sigma <= 1e-5 (small) and 2e-5 (multi-tile),
+  energies <= 1e-4 Eh (BF16X3) and 5e-5 Eh (BF16X6) -- so that a regression
+  shows; they are not a claim that the targets are met.
+Plain BF16 is held to relative error <= 3e-2."""
 import os
 
 import numpy as np
