@@ -189,7 +189,8 @@ def run_mine(args):
     h, L, bonds, path = make_inputs(w, td, k)
     plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=prec, tol=args.tol, max_iter=args.dav_iters,
                   keep_envs=0, fp64_store=int(args.fp64_store), refine=int(args.refine),
-                  fp64_tc=int(args.fp64_tc))
+                  fp64_tc=int(args.fp64_tc), scratch_bytes=int(args.scratch_gb * 2**30),
+                  mem_budget=int(args.mem_budget_gb * 2**30))
     stream = torch.cuda.Stream()
     plan.set_bond(k, stream=stream)
     dim = plan.dim
@@ -293,7 +294,7 @@ def run_mine(args):
     # end-to-end through the host-buffer C-ABI call: each step copies its guess
     # from pinned host memory, runs Davidson and the decimation, and reads the
     # next bond's guess back into pinned host memory
-    n_e2e = max(3, args.e2e_steps)
+    n_e2e = max(3, args.e2e_steps) if args.e2e_steps > 0 else 0
     cap = 4 * x.numel() + 64
     hbuf = [torch.empty(cap, dtype=torch.float64).pin_memory(), torch.empty(cap, dtype=torch.float64).pin_memory()]
     hbuf[0][:x.numel()].copy_(x.cpu())
@@ -310,10 +311,10 @@ def run_mine(args):
         h2d += cur * 8
         d2h += nd * 8
         cur = nd
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = (time.perf_counter() - t0) / max(n_e2e, 1)
     s_e1 = plan.stats()
-    e2e_flops = (flop_counters(s_e1) - flop_counters(s_e0)) / n_e2e
-    e2e_value = world * e2e_flops / e2e_s / 1e12
+    e2e_flops = (flop_counters(s_e1) - flop_counters(s_e0)) / max(n_e2e, 1)
+    e2e_value = world * e2e_flops / e2e_s / 1e12 if n_e2e > 0 else None
     st_end = plan.stats()
     launches = s_after["kernel_launches"] - s_before["kernel_launches"]
     n_conv = sum(1 for d in dav_timed if d[1])
@@ -359,23 +360,82 @@ def run_mine(args):
                                f"{d_n} calls in the timed steps, {d_ms / max(d_n, 1):.1f} ms each)",
                      "traffic_note": "no DRAM counters at this size (captures with more than the launch list are "
                                      "taken on a few-GB workload only); see profiles/"},
-        "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "steps": n_e2e,
+        "e2e": {"value": round(e2e_value, 3) if e2e_value is not None else None, "unit": "TFLOP/s", "steps": n_e2e,
                 "call": "dmrg_update_bond_host (pinned host guess in, next guess out)",
-                "h2d_bytes_per_step": int(h2d / n_e2e), "d2h_bytes_per_step": int(d2h / n_e2e)},
+                "h2d_bytes_per_step": int(h2d / max(n_e2e, 1)), "d2h_bytes_per_step": int(d2h / max(n_e2e, 1))},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "device_bytes": st_end["device_bytes"],
     }
+    plan.close()
+    del plan
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if args.fp64_check:
+        out["accuracy_vs_fp64"] = accuracy_leg(g, torch, w, h, L, path, k, args)
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, cores = oracle_sample_rate(3)
         out["cpu_baseline"] = {"value": rate, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                                "sample": f"oracle sigma at K={CPU_SAMPLE['K']}, D={CPU_SAMPLE['D']} middle bond "
                                          f"(same recipe), {dt:.2f} s per sigma, FLOPs of the oracle's own products"}
-    plan.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def accuracy_leg(g, torch, w, h, L, path, k, args):
+    """Mixed against FP64 at the middle bond of the workload (the seeded MPS of
+    the timed run), in the mode that meets the energy target: BF16X3 sigma over
+    an FP64 operator store renormalised on the FP64 tensor-core engine.
+
+    1. the plain mixed Davidson (stops at its noise floor): its energy against
+       the FP64 Rayleigh quotient of its own vector (FP64 tensor-core sigma);
+    2. from there, the FP64 residual correction to |r| <= tol (timed);
+    3. the FP64 sigma of the corrected vector on the FP64 arithmetic units
+       (the plain FP64 GPU path, independent of the tensor-core emulation): its
+       Rayleigh quotient and residual.  |E - lambda| <= |r|^2 / gap for the
+       FP64 eigenvalue lambda nearest E."""
+    free = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    plan = g.Plan(h, L, w["K"], w["N"], w["twoS"], w["D"], path, precision=PRECISIONS["bf16x3"], fp64_store=1,
+                  fp64_tc=1, refine=0, tol=args.tol, max_iter=args.dav_iters, keep_envs=0,
+                  scratch_bytes=int(max(args.scratch_gb, 6.0) * 2**30), mem_budget=int(0.97 * free))
+    plan.set_bond(k)
+    setup = time.perf_counter() - t0
+    x = torch.from_numpy(si.random_vector(plan.dim, seed=5)).cuda()
+    t1 = time.perf_counter()
+    em, itm, _ = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters)
+    t2 = time.perf_counter()
+    wv = torch.empty_like(x)
+    plan.sigma_fp64(x, wv)
+    nrm2 = float(x @ x)
+    rq_m = float(x @ wv) / nrm2
+    res_m = float(torch.linalg.vector_norm(wv - rq_m * x)) / nrm2 ** 0.5
+    plan.set_refine(1, 8)
+    t3 = time.perf_counter()
+    er, itr, convr = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    st = plan.stats()
+    plan.sigma_fp64_units(x, wv)
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    nrm2 = float(x @ x)
+    rq = float(x @ wv) / nrm2
+    res = float(torch.linalg.vector_norm(wv - rq * x)) / nrm2 ** 0.5
+    out = {"bond": k, "dim": plan.dim, "setup_s": round(setup, 1),
+           "mixed": {"energy": float(em[0]), "fp64_rq": rq_m, "dE": float(em[0]) - rq_m, "fp64_residual": res_m,
+                     "iterations": itm, "seconds": round(t2 - t1, 2)},
+           "refined": {"energy": float(er[0]), "converged": bool(convr), "iterations": itr,
+                       "rounds": st["davidson_refine_last"], "fp64_residual_reported": st["davidson_rnorm_last"],
+                       "seconds": round(t4 - t3, 2)},
+           "fp64_units": {"rq": rq, "residual": res, "dE_refined": float(er[0]) - rq,
+                          "eigenvalue_error_times_gap_bound": res * res, "sigma_s": round(t5 - t4, 2)},
+           "within_1e-6": abs(float(er[0]) - rq) <= 1e-6 and res * res <= 1e-8,
+           "mode": "bf16x3 sigma, FP64 store (FP64 tensor-core engine), FP64 residual correction"}
+    plan.close()
+    return out
 
 
 def run_sigma_probe(args):
@@ -432,6 +492,69 @@ def run_sigma_probe(args):
     plan.close()
 
 
+def run_mlp_study(args):
+    """--mlp-study: the learned Davidson preconditioner at the workload's middle
+    bonds.  Pairs are harvested by plain Jacobi Davidson (with Jacobi-Davidson
+    correction equations solved by MINRES) from --mlp-guesses random guesses at
+    the middle bond (in --precision), the network is trained (weighted loss,
+    held-out tenth), and Davidson to |r| <= --tol runs with Jacobi and with the
+    trained network from the same guess at three bonds (in
+    --mlp-eval-precision, FP64-accurate by default, so that the residual can
+    reach the tolerance).  Prints one JSON line (not the benchmark contract
+    line)."""
+    import torch
+    import paper_2311_02854_gb300 as g
+
+    w = WORKLOADS[args.workload]
+    K, D = w["K"], w["D"]
+    kmid = K // 2
+    prec = PRECISIONS[args.precision]
+    td = tempfile.mkdtemp(prefix="dmrg_mlp_")
+    t0 = time.time()
+    h, L, bonds, path = make_inputs(w, td, kmid)
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=prec, fp64_store=int(args.fp64_store),
+                  fp64_tc=int(args.fp64_tc))
+    plan.set_bond(kmid)
+    plan.mlp_init(3)
+    pairs = 0
+    for seed in range(11, 11 + args.mlp_guesses):
+        x = torch.from_numpy(si.random_vector(plan.dim, seed=seed)).cuda()
+        _, n = plan.mlp_harvest(x, max_iter=15, jd_iters=40, per_solve=args.mlp_per_solve)
+        pairs += n
+    t_harvest = time.time() - t0
+    l0, l1, h0, h1 = plan.mlp_train(steps=args.mlp_steps, batch=8192, lr=2e-3, seed=7, held_out=True)
+    params = plan.mlp_params()
+    plan.close()
+    rows = []
+    for k in (kmid - 1, kmid, kmid + 1):
+        mps = si.random_mps(K, w["N"], w["twoS"], bonds, center=k, seed=2)
+        pk = os.path.join(td, f"mps_{k}.bin")
+        si.write_mps(pk, mps)
+        p2 = g.Plan(h, L, K, w["N"], w["twoS"], D, pk, precision=PRECISIONS[args.mlp_eval_precision])
+        p2.set_bond(k)
+        p2.mlp_params(params)
+        guess = si.random_vector(p2.dim, seed=1)
+        row = {"bond": k}
+        for name, pc in (("jacobi", 0), ("mlp", 1)):
+            x = torch.from_numpy(guess.copy()).cuda()
+            t1 = time.time()
+            e, it, conv = p2.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters, precond=pc)
+            row[name] = {"iterations": it, "converged": bool(conv), "energy": float(e[0]),
+                         "seconds": round(time.time() - t1, 2)}
+        row["dE"] = row["mlp"]["energy"] - row["jacobi"]["energy"]
+        row["fallbacks"] = p2.stats()["precond_fallbacks"]
+        rows.append(row)
+        p2.close()
+    ij = sum(r["jacobi"]["iterations"] for r in rows)
+    im = sum(r["mlp"]["iterations"] for r in rows)
+    print(json.dumps({"mode": "mlp-study", "workload": args.workload, "precision": args.precision,
+                      "eval_precision": args.mlp_eval_precision, "pairs": pairs,
+                      "harvest_s": round(t_harvest, 1),
+                      "loss": {"train_first": l0, "train_last": l1, "held_out_before": h0, "held_out_after": h1},
+                      "bonds": rows, "iterations_jacobi": ij, "iterations_mlp": im,
+                      "ratio_mlp_over_jacobi": im / max(ij, 1)}), flush=True)
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -469,20 +592,32 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS))
     ap.add_argument("--dav-iters", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (>= 3; 0 skips, for probes)")
     ap.add_argument("--fp64-store", type=int, default=0, help="mixed modes: keep the FP64 operator store")
     ap.add_argument("--refine", type=int, default=0, help="mixed modes: FP64 residual correction of Davidson")
+    ap.add_argument("--scratch-gb", type=float, default=0.0, help="sigma scratch per chunk (0: automatic)")
+    ap.add_argument("--mem-budget-gb", type=float, default=0.0, help="device bytes the plan may hold (0: 90%% of free)")
+    ap.add_argument("--fp64-check", type=int, default=1,
+                    help="after the timed steps: one Davidson in the timed mode and the FP64-unit sigma of its vector")
     ap.add_argument("--fp64-tc", type=int, default=0,
                     help="mixed modes with --fp64-store 1: FP64 products on the FP64-accurate tensor-core engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvec", type=int, default=1, help="--sigma-only: vectors per grouped sigma launch")
     ap.add_argument("--sigma-only", action="store_true",
                     help="time sigma calls at the middle bond (NVTX range 'sigma'); for profiling")
+    ap.add_argument("--mlp-study", action="store_true",
+                    help="learned preconditioner: harvest, train, Davidson iterations against Jacobi at 3 bonds")
+    ap.add_argument("--mlp-guesses", type=int, default=4)
+    ap.add_argument("--mlp-per-solve", type=int, default=16384)
+    ap.add_argument("--mlp-steps", type=int, default=2000)
+    ap.add_argument("--mlp-eval-precision", default="fp64tc", choices=sorted(PRECISIONS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.sigma_only:
         run_sigma_probe(args)
+    elif args.mlp_study:
+        run_mlp_study(args)
     else:
         run_mine(args)
 

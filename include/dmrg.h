@@ -267,6 +267,11 @@ dmrg_status dmrg_hdiag(dmrg_plan_t plan, double* diag_dev, void* stream);
 dmrg_status dmrg_davidson(dmrg_plan_t plan, double* psi_dev, int n_roots, double tol, int max_iter,
                           int precond, double* energies, int* iters, void* stream);
 
+/* Switch the FP64 residual correction of later dmrg_davidson calls (the
+ * refine / max_refine options; mixed modes only).  DMRG_EINVAL for a negative
+ * max_refine. */
+dmrg_status dmrg_set_refine(dmrg_plan_t plan, int refine, int max_refine);
+
 /* One two-site bond update (Sec. 2.1, Fig. flowchart) from HOST buffers, the
  * end-to-end path of a caller that keeps its vectors in host memory:
  *  psi_host   n_roots guesses of the current bond (host, FP64, canonical
@@ -348,25 +353,33 @@ dmrg_status dmrg_mlp_init(dmrg_plan_t plan, uint32_t seed);
  * the Ritz vector); at every iteration the Jacobi-Davidson correction
  * equation of root 0 is solved by MINRES (jd_iters iterations at most), and
  * up to per_solve strided elements give training pairs (features, target
- * g_i = -t_i (H_ii - theta)/r_i, clipped to [-10, 10]) appended to the plan's
- * training set.  *n_pairs receives the number added. */
+ * g_i = -t_i (H_ii - theta)/r_i, clipped to [-10, 10], weight
+ * (r_i / (H_ii - theta))^2 scaled to mean 1 over the solve: the weighted
+ * squared error of g is the squared error of the correction t) appended to
+ * the plan's training set.  *n_pairs receives the number added. */
 dmrg_status dmrg_mlp_harvest(dmrg_plan_t plan, double* psi_dev, int max_iter, int jd_iters, int64_t per_solve,
                              double* energy, int64_t* n_pairs, void* stream);
 
 /* steps Adam steps (learning rate lr) on batches of `batch` pairs drawn from
- * the training set by a seeded counter-based generator; loss (mean squared
- * error of g) of the first and last batch.  Marks the network trained. */
+ * the first nine tenths of the training set by a seeded counter-based
+ * generator; the last tenth (the latest solves) is held out.  Loss = weighted
+ * mean squared error of g (weights of dmrg_mlp_harvest).  Out (host, each may
+ * be NULL): loss of the first and last training batch, loss of the held-out
+ * pairs before and after training (0 with fewer than 20 pairs).  Marks the
+ * network trained. */
 dmrg_status dmrg_mlp_train(dmrg_plan_t plan, int steps, int64_t batch, float lr, uint64_t seed,
-                           float* loss_first, float* loss_last, void* stream);
+                           float* loss_first, float* loss_last, float* held_first, float* held_last,
+                           void* stream);
 
 /* g_dev[i] = g(x_dev[5i .. 5i+4]) for n rows (device FP32); bf16 selects the
  * inference weights. */
 dmrg_status dmrg_mlp_eval(dmrg_plan_t plan, const float* x_dev, int64_t n, float* g_dev, int bf16, void* stream);
 
-/* Gradient of (1/n) sum_i (g(x_i) - y_i)^2 with respect to the parameters
- * (layout of dmrg_mlp_params) into grad_dev, the loss into loss_dev (device). */
-dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x_dev, const float* y_dev, int64_t n,
-                              float* grad_dev, float* loss_dev, void* stream);
+/* Gradient of (1/n) sum_i w_i (g(x_i) - y_i)^2 with respect to the parameters
+ * (layout of dmrg_mlp_params) into grad_dev, the loss into loss_dev (device);
+ * w_dev may be NULL (all weights 1). */
+dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x_dev, const float* y_dev, const float* w_dev,
+                              int64_t n, float* grad_dev, float* loss_dev, void* stream);
 
 /* Parameters (host, dmrg_mlp_num_params() floats: W1[64x5], b1[64],
  * W2[64x64], b2[64], W3[64], b3): get (set = 0) or set (set = 1; marks the

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE (see oracle/__init__.py): only tests/ may use it.  The
 paper has no learned part; this restates the network the library trains:
 g(x) = W3 . tanh(W2 tanh(W1 x + b1) + b2) + b3 with x in R^5, 64 hidden units
-per layer, and the gradient of the mean squared error of g against targets y.
+per layer, and the gradient of the (weighted) mean squared error of g against
+targets y.
 Parameters are one flat vector in the order W1 (64 x 5, row-major), b1 (64),
 W2 (64 x 64), b2 (64), W3 (64), b3 (1).
 
@@ -37,14 +38,16 @@ def forward(theta, X):
     return g, h1, h2
 
 
-def loss_and_grad(theta, X, y):
-    """L = mean((g - y)^2) and dL/dtheta (flat), by the chain rule layer by layer."""
+def loss_and_grad(theta, X, y, w=None):
+    """L = mean(w (g - y)^2) (w = 1 when None) and dL/dtheta (flat), by the
+    chain rule layer by layer."""
     p = unpack(theta)
     g, h1, h2 = forward(theta, X)
     n = X.shape[0]
+    w = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
     e = g - y
-    L = float(np.mean(e * e))
-    dg = 2.0 * e / n                       # dL/dg
+    L = float(np.mean(w * e * e))
+    dg = 2.0 * w * e / n                   # dL/dg
     gW3 = h2.T @ dg
     gb3 = np.array([dg.sum()])
     dz2 = np.outer(dg, p["W3"]) * (1.0 - h2 * h2)

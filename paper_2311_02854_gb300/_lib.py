@@ -82,6 +82,7 @@ _SIGS = {
     "dmrg_davidson": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_int, C.c_int, _D, _I, _P]),
     "dmrg_decimate": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _D, _P, _L, _P]),
     "dmrg_update_bond_host": (C.c_int, [_P, _D, C.c_int, C.c_int, C.c_int, _D, _I, _D, _D, _L, _P]),
+    "dmrg_set_refine": (C.c_int, [_P, C.c_int, C.c_int]),
     "dmrg_sweep": (C.c_int, [_P, C.c_int, _I, _D, _D, _P]),
     "dmrg_save_mps": (C.c_int, [_P, C.c_char_p]),
     "dmrg_stats": (C.c_int, [_P, C.POINTER(Stats)]),
@@ -95,9 +96,9 @@ _SIGS = {
     "dmrg_mlp_init": (C.c_int, [_P, C.c_uint32]),
     "dmrg_mlp_harvest": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _D, _L, _P]),
     "dmrg_mlp_train": (C.c_int, [_P, C.c_int, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_float),
-                                 C.POINTER(C.c_float), _P]),
+                                 C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float), _P]),
     "dmrg_mlp_eval": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, _P]),
-    "dmrg_mlp_gradient": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "dmrg_mlp_gradient": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P, _P]),
     "dmrg_mlp_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "dmrg_mlp_num_params": (C.c_int, []),
     "dmrg_extrapolate": (C.c_int, [_D, _D, C.c_int, _D, _D, _D]),
@@ -247,6 +248,9 @@ class Plan:
                    _ptr(next_psi), C.byref(nd), _stream(stream))
         return float(w[0]), nd.value
 
+    def set_refine(self, refine, max_refine=0):
+        self._call("dmrg_set_refine", int(bool(refine)), int(max_refine))
+
     def update_bond_host(self, psi, n_roots, D, forward, next_psi=None, stream=None):
         """dmrg_update_bond_host: Davidson + decimation from host buffers (numpy
         FP64 arrays; pinned memory if they view a pinned torch tensor).  Returns
@@ -298,11 +302,15 @@ class Plan:
                    C.byref(n), _stream(stream))
         return e.value, n.value
 
-    def mlp_train(self, steps=400, batch=4096, lr=3e-3, seed=3, stream=None):
-        """Adam on the collected pairs; returns (first, last) batch loss."""
-        l0, l1 = C.c_float(0.0), C.c_float(0.0)
+    def mlp_train(self, steps=400, batch=4096, lr=3e-3, seed=3, stream=None, held_out=False):
+        """Adam on the collected pairs (weighted loss); returns the (first, last)
+        training-batch loss, and with held_out=True also the (before, after)
+        loss of the held-out last tenth of the pairs."""
+        l0, l1, h0, h1 = C.c_float(0.0), C.c_float(0.0), C.c_float(0.0), C.c_float(0.0)
         self._call("dmrg_mlp_train", int(steps), int(batch), float(lr), int(seed), C.byref(l0), C.byref(l1),
-                   _stream(stream))
+                   C.byref(h0), C.byref(h1), _stream(stream))
+        if held_out:
+            return l0.value, l1.value, h0.value, h1.value
         return l0.value, l1.value
 
     def mlp_eval(self, x, g, bf16=False, stream=None):
@@ -310,9 +318,9 @@ class Plan:
         n = int(x.numel() // 5)
         self._call("dmrg_mlp_eval", _ptr(x), n, _ptr(g), int(bool(bf16)), _stream(stream))
 
-    def mlp_gradient(self, x, y, grad, loss, stream=None):
+    def mlp_gradient(self, x, y, grad, loss, w=None, stream=None):
         n = int(x.numel() // 5)
-        self._call("dmrg_mlp_gradient", _ptr(x), _ptr(y), n, _ptr(grad), _ptr(loss), _stream(stream))
+        self._call("dmrg_mlp_gradient", _ptr(x), _ptr(y), _ptr(w), n, _ptr(grad), _ptr(loss), _stream(stream))
 
     def mlp_params(self, values=None):
         """Get (values None) or set the FP32 parameters (numpy float32 array)."""

@@ -339,6 +339,12 @@ int64_t scratch_cap(const Plan& P) {
     return cap;
 }
 
+int64_t scratch_cap_f64(const Plan& P) {
+    int64_t cap = P.opt.scratch_bytes > 0 ? P.opt.scratch_bytes / 8 : 0;
+    if (cap <= 0) cap = std::max<int64_t>((int64_t)1 << 26, P.budget / 8 / 12);
+    return cap;
+}
+
 // ---------------------------------------------------------------------------
 // Intermediates: Int[rows x nnz] = W[rows x nops] * Family[nops x nnz]
 // ---------------------------------------------------------------------------
@@ -649,7 +655,7 @@ std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward)
     }
     int maxd = std::max({XL.basis.dmax(), OL.basis.dmax(), 1});
     ensure_ident(P, maxd);
-    const int64_t cap = scratch_cap(P);
+    const int64_t cap = P.tc_store() ? scratch_cap(P) : scratch_cap_f64(P);
     if (P.tc_store()) {
         // the cp.async-staged engine: renormalisation lists hold many short
         // products (K-chunks of 256), where it measured faster than the
@@ -1091,7 +1097,7 @@ void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t 
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
     if (!P.sigma_fp64_ready) {
         P.f64_tiles(P.sigma_pl);
-        P.sigma_pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap(P) / 2, 1 << 24), kChunkF64);
+        P.sigma_pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap_f64(P) / 2, 1 << 24), kChunkF64);
         ensure_scratch_f64(P, std::max<int64_t>(P.sigma_pl.scratch_elems, 1));
         P.sigma_pl.upload(st);
         P.sigma_fp64_ready = true;
@@ -1128,7 +1134,7 @@ void sigma_fp64_units(Plan& P, const double* psi, double* out, int nvec, cudaStr
         pl.outs = P.sigma_pl.outs;
         pl.cs = P.sigma_pl.cs;
         pl.tile_m = pl.tile_n = 0;  // 64 x 64 tiles: the FP64 units
-        pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap(P) / 2, 1 << 24), kChunkF64);
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, std::max<int64_t>(scratch_cap_f64(P) / 2, 1 << 24), kChunkF64);
         pl.upload(st);
         P.sigma_units_ready = true;
     }

@@ -11,7 +11,8 @@ void free_block(Plan& P, std::unique_ptr<Block>& b);
 void ensure_ident(Plan& P, int n);
 void ensure_scratch(Plan& P, int64_t n);      // scratch of the plan's engine
 void ensure_scratch_f64(Plan& P, int64_t n);  // FP64 scratch (FP64 engine in either mode)
-int64_t scratch_cap(const Plan& P);
+int64_t scratch_cap(const Plan& P);      // scratch elements of the plan's engine
+int64_t scratch_cap_f64(const Plan& P);  // scratch elements of FP64-engine lists
 std::unique_ptr<Block> make_vacuum(Plan& P, bool right_end);
 Basis bond_basis(const Plan& P, int b, bool right_side);
 std::unique_ptr<Block> renormalise(Plan& P, const Block& X, int m, bool forward);

@@ -412,14 +412,14 @@ dmrg_status dmrg_mlp_harvest(dmrg_plan_t plan, double* psi, int max_iter, int jd
 }
 
 dmrg_status dmrg_mlp_train(dmrg_plan_t plan, int steps, int64_t batch, float lr, uint64_t seed, float* loss_first,
-                           float* loss_last, void* stream) {
+                           float* loss_last, float* held_first, float* held_last, void* stream) {
     if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
     if (steps < 1 || batch < 1 || !(lr > 0.f)) return fail(plan, DMRG_EINVAL, "bad arguments");
     return guarded(plan, [&]() {
         cudaStream_t st = pick(plan, stream);
         Plan& P = plan->P;
         if (!P.mlp.d_w) mlp_init(P.mlp, 3u, st);
-        mlp_train(P.mlp, steps, batch, lr, seed, loss_first, loss_last, st);
+        mlp_train(P.mlp, steps, batch, lr, seed, loss_first, loss_last, held_first, held_last, st);
         return DMRG_OK;
     });
 }
@@ -437,15 +437,15 @@ dmrg_status dmrg_mlp_eval(dmrg_plan_t plan, const float* x, int64_t n, float* g,
     });
 }
 
-dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x, const float* y, int64_t n, float* grad, float* loss,
-                              void* stream) {
+dmrg_status dmrg_mlp_gradient(dmrg_plan_t plan, const float* x, const float* y, const float* w, int64_t n,
+                              float* grad, float* loss, void* stream) {
     if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
     if (!x || !y || !grad || !loss || n < 1) return fail(plan, DMRG_EINVAL, "bad arguments");
     return guarded(plan, [&]() {
         cudaStream_t st = pick(plan, stream);
         Plan& P = plan->P;
         DMRG_REQUIRE(P.mlp.d_w, DMRG_EINVAL, "MLP not initialised (dmrg_mlp_init)");
-        mlp_gradient(P.mlp, x, y, n, grad, loss, st);
+        mlp_gradient(P.mlp, x, y, w, n, grad, loss, st);
         DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
         return DMRG_OK;
     });
@@ -489,6 +489,14 @@ dmrg_status dmrg_decimate(dmrg_plan_t plan, const double* psi, int n_roots, int 
         DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
         return DMRG_OK;
     });
+}
+
+dmrg_status dmrg_set_refine(dmrg_plan_t plan, int refine, int max_refine) {
+    if (!plan) return fail(nullptr, DMRG_EINVAL, "plan is NULL");
+    if (max_refine < 0) return fail(plan, DMRG_EINVAL, "max_refine must be >= 0");
+    plan->P.opt.refine = refine != 0;
+    plan->P.opt.max_refine = max_refine;
+    return DMRG_OK;
 }
 
 dmrg_status dmrg_update_bond_host(dmrg_plan_t plan, const double* psi_host, int n_roots, int D, int forward,

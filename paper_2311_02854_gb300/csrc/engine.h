@@ -80,6 +80,7 @@ void launch_seg_gemm_f64(const WorkList& w, const BufTable& bt, int nvec, cudaSt
 void launch_seg_gemm_oz(const WorkList& w, const BufTable& bt, int nvec, int* d_err, cudaStream_t st);
 int oz_tile_rows();
 int oz_tile_cols();
+int oz_stage_depth();
 // device error word of the FP64 tensor-core engine (set when a bounded wait
 // gave up); oz_take_error reads and clears it (synchronises the stream)
 int* oz_error_word();

@@ -68,6 +68,26 @@ void WorkList::add_block(int64_t c_off, int c_buf, int m, int n, int ldc, const 
 }
 
 void WorkList::upload(cudaStream_t st) {
+    if (tile_m == oz_tile_rows() && tiles.size() > 1) {
+        // the tensor-core engine's persistent CTAs take tiles round-robin: longest
+        // first (stable counting sort on the stage count), so that short tiles
+        // fill in at the end instead of a few long ones trailing
+        const int tk = oz_stage_depth();
+        std::vector<int> nst(tiles.size());
+        int maxn = 0;
+        for (size_t i = 0; i < tiles.size(); ++i) {
+            int64_t n = 0;
+            for (int s = tiles[i].seg_beg; s < tiles[i].seg_end; ++s) n += (segs[s].k + tk - 1) / tk;
+            nst[i] = (int)std::min<int64_t>(n, 1 << 20);
+            maxn = std::max(maxn, nst[i]);
+        }
+        std::vector<size_t> pos((size_t)maxn + 2, 0);
+        for (int n : nst) ++pos[(size_t)(maxn - n) + 1];
+        for (size_t i = 1; i < pos.size(); ++i) pos[i] += pos[i - 1];
+        std::vector<Tile> sorted(tiles.size());
+        for (size_t i = 0; i < tiles.size(); ++i) sorted[pos[(size_t)(maxn - nst[i])]++] = tiles[i];
+        tiles.swap(sorted);
+    }
     if (tiles.size() > cap_tiles) {
         if (d_tiles) cudaFree(d_tiles);
         cap_tiles = tiles.size() + tiles.size() / 4 + 16;

@@ -87,14 +87,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // splitmix64 finaliser
 }
 
 // Per sample b of a batch (row idx(b) of the set; identity when seed == 0):
-// forward, then dg = 2(g - y)/B, dz2 = dg W3 (1 - h2^2), dz1 = (W2^T dz2)(1 - h1^2).
+// forward, then dg = 2 w (g - y)/B (w = 1 without weights), dz2 = dg W3 (1 - h2^2),
+// dz1 = (W2^T dz2)(1 - h1^2).
 // work rows: [h1 (64) | h2 (64) | dz1 (64) | dz2 (64) | dg | x (5)]
 constexpr int kWorkRow = 4 * kMlpHid + 1 + kMlpIn;
 
 __global__ void __launch_bounds__(NT) backward_kernel(const float* __restrict__ w, const float* __restrict__ x,
-                                                      const float* __restrict__ y, int64_t n_set, int64_t B,
-                                                      uint64_t seed, float* __restrict__ work,
-                                                      float* __restrict__ loss) {
+                                                      const float* __restrict__ y, const float* __restrict__ wt,
+                                                      int64_t n_set, int64_t B, uint64_t seed,
+                                                      float* __restrict__ work, float* __restrict__ loss) {
     __shared__ float sw[kMlpParams];
     __shared__ float red[NT];
     load_params(sw, w, nullptr, false);
@@ -114,8 +115,9 @@ __global__ void __launch_bounds__(NT) backward_kernel(const float* __restrict__ 
         }
         const float g = mlp_eval(sw, xi, h1, h2);
         const float e = g - y[idx];
-        lsum += e * e;
-        const float dg = 2.f * e / (float)B;
+        const float wi = wt ? wt[idx] : 1.f;
+        lsum += wi * e * e;
+        const float dg = 2.f * wi * e / (float)B;
         row[4 * kMlpHid] = dg;
         for (int j = 0; j < kMlpHid; ++j) dz2[j] = dg * sw[kMlpOffW3 + j] * (1.f - h2[j] * h2[j]);
         for (int i = 0; i < kMlpHid; ++i) {
@@ -183,7 +185,7 @@ __global__ void collect_kernel(const double* __restrict__ hd, const double* __re
                                const double* __restrict__ t, double theta, double s, double rmax, int64_t n,
                                int64_t stride, int64_t take, const int64_t* __restrict__ sec_off,
                                const float* __restrict__ sec_q, int nsec, int* __restrict__ flag,
-                               float* __restrict__ xs, float* __restrict__ ys) {
+                               float* __restrict__ xs, float* __restrict__ ys, float* __restrict__ ws) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= take) return;
     const int64_t i = k * stride;
@@ -204,16 +206,21 @@ __global__ void collect_kernel(const double* __restrict__ hd, const double* __re
     xs[k * kMlpIn + 4] = sec_q[2 * lo + 1];
     const double g = -t[i] * d / r[i];
     ys[k] = (float)fmin(fmax(g, -10.0), 10.0);
+    // weight of the pair: an error dg in g moves the correction by dg r_i / (H_ii - theta)
+    const double q = r[i] / d;
+    ws[k] = (float)fmin(q * q, 1e30);
 }
 
 __global__ void compact_kernel(const int* __restrict__ pos, const int* __restrict__ flag, int64_t take,
-                               const float* __restrict__ xs, const float* __restrict__ ys, float* __restrict__ x,
-                               float* __restrict__ y) {
+                               const float* __restrict__ xs, const float* __restrict__ ys,
+                               const float* __restrict__ ws, float wscale, float* __restrict__ x,
+                               float* __restrict__ y, float* __restrict__ w) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= take || !flag[k]) return;
     const int64_t p = pos[k];
     for (int c = 0; c < kMlpIn; ++c) x[p * kMlpIn + c] = xs[k * kMlpIn + c];
     y[p] = ys[k];
+    w[p] = ws[k] * wscale;
 }
 
 uint64_t mix64_host(uint64_t z) {
@@ -245,12 +252,12 @@ int grid_n(int64_t n) {
 }  // namespace
 
 void Mlp::release() {
-    for (void* p : {(void*)d_w, (void*)d_wb, (void*)d_adam, (void*)d_grad, (void*)d_x, (void*)d_y, (void*)d_work,
-                    (void*)d_sec_off, (void*)d_sec_q})
+    for (void* p : {(void*)d_w, (void*)d_wb, (void*)d_adam, (void*)d_grad, (void*)d_x, (void*)d_y, (void*)d_wt,
+                    (void*)d_work, (void*)d_sec_off, (void*)d_sec_q})
         if (p) cudaFree(p);
     d_w = nullptr;
     d_wb = nullptr;
-    d_adam = d_grad = d_x = d_y = d_work = d_sec_q = nullptr;
+    d_adam = d_grad = d_x = d_y = d_wt = d_work = d_sec_q = nullptr;
     d_sec_off = nullptr;
     n_set = cap_set = cap_work = 0;
     n_sec = 0;
@@ -308,12 +315,12 @@ void ensure_work(Mlp& m, int64_t B) {
     DMRG_CHECK_CUDA(cudaMalloc(&m.d_work, (size_t)B * kWorkRow * sizeof(float)));
 }
 
-void gradient_batch(Mlp& m, const float* x, const float* y, int64_t n_set, int64_t B, uint64_t seed, float* grad,
-                    float* loss, cudaStream_t st) {
+void gradient_batch(Mlp& m, const float* x, const float* y, const float* wt, int64_t n_set, int64_t B,
+                    uint64_t seed, float* grad, float* loss, cudaStream_t st) {
     ensure_work(m, B);
     DMRG_CHECK_CUDA(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), st));
     DMRG_CHECK_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
-    backward_kernel<<<grid_n(B), NT, 0, st>>>(m.d_w, x, y, n_set, B, seed, m.d_work, loss);
+    backward_kernel<<<grid_n(B), NT, 0, st>>>(m.d_w, x, y, wt, n_set, B, seed, m.d_work, loss);
     const int64_t chunk = 1024;
     const unsigned nch = (unsigned)((B + chunk - 1) / chunk);
     // W3 / b3: dg (column 256) x h2 (columns 64..127)
@@ -330,8 +337,9 @@ void gradient_batch(Mlp& m, const float* x, const float* y, int64_t n_set, int64
 }
 }  // namespace
 
-void mlp_gradient(Mlp& m, const float* x, const float* y, int64_t n, float* grad, float* loss, cudaStream_t st) {
-    gradient_batch(m, x, y, n, n, 0, grad, loss, st);
+void mlp_gradient(Mlp& m, const float* x, const float* y, const float* w, int64_t n, float* grad, float* loss,
+                  cudaStream_t st) {
+    gradient_batch(m, x, y, w, n, n, 0, grad, loss, st);
 }
 
 void mlp_adam(Mlp& m, float lr, cudaStream_t st) {
@@ -377,40 +385,52 @@ int64_t mlp_collect(Mlp& m, const double* hd, const double* r, const double* t, 
     const int64_t stride = std::max<int64_t>(1, n / take);
     if (m.n_set + take > m.cap_set) {  // grow the set
         const int64_t cap = std::max<int64_t>(2 * m.cap_set, m.n_set + take);
-        float *nx = nullptr, *ny = nullptr;
+        float *nx = nullptr, *ny = nullptr, *nw = nullptr;
         DMRG_CHECK_CUDA(cudaMalloc(&nx, (size_t)cap * kMlpIn * sizeof(float)));
         DMRG_CHECK_CUDA(cudaMalloc(&ny, (size_t)cap * sizeof(float)));
+        DMRG_CHECK_CUDA(cudaMalloc(&nw, (size_t)cap * sizeof(float)));
         if (m.n_set > 0) {
             DMRG_CHECK_CUDA(cudaMemcpyAsync(nx, m.d_x, (size_t)m.n_set * kMlpIn * sizeof(float),
                                             cudaMemcpyDeviceToDevice, st));
             DMRG_CHECK_CUDA(cudaMemcpyAsync(ny, m.d_y, (size_t)m.n_set * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            DMRG_CHECK_CUDA(cudaMemcpyAsync(nw, m.d_wt, (size_t)m.n_set * sizeof(float), cudaMemcpyDeviceToDevice, st));
         }
         DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
         cudaFree(m.d_x);
         cudaFree(m.d_y);
+        if (m.d_wt) cudaFree(m.d_wt);
         m.d_x = nx;
         m.d_y = ny;
+        m.d_wt = nw;
         m.cap_set = cap;
     }
     int* flag = nullptr;
-    float *xs = nullptr, *ys = nullptr;
+    float *xs = nullptr, *ys = nullptr, *ws = nullptr;
     DMRG_CHECK_CUDA(cudaMalloc(&flag, (size_t)take * 2 * sizeof(int)));
-    DMRG_CHECK_CUDA(cudaMalloc(&xs, (size_t)take * (kMlpIn + 1) * sizeof(float)));
+    DMRG_CHECK_CUDA(cudaMalloc(&xs, (size_t)take * (kMlpIn + 2) * sizeof(float)));
     ys = xs + (size_t)take * kMlpIn;
+    ws = ys + take;
     const int blocks = (int)((take + NT - 1) / NT);
     collect_kernel<<<blocks, NT, 0, st>>>(hd, r, t, theta, s > 0 ? s : 1.0, rmax > 0 ? rmax : 1.0, n, stride, take,
-                                          m.d_sec_off, m.d_sec_q, m.n_sec, flag, xs, ys);
+                                          m.d_sec_off, m.d_sec_q, m.n_sec, flag, xs, ys, ws);
     ++launch_counter();
     std::vector<int> hf(take), pos(take);
+    std::vector<float> hw(take);
     DMRG_CHECK_CUDA(cudaMemcpyAsync(hf.data(), flag, take * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DMRG_CHECK_CUDA(cudaMemcpyAsync(hw.data(), ws, take * sizeof(float), cudaMemcpyDeviceToHost, st));
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
     int64_t cnt = 0;
+    double wsum = 0.0;
     for (int64_t k = 0; k < take; ++k) {
         pos[k] = (int)(m.n_set + cnt);
         cnt += hf[k];
+        if (hf[k]) wsum += hw[k];
     }
+    // every solve's pairs carry weights of mean 1, so each correction equation
+    // counts alike whatever the scale of its residual
+    const float wscale = (cnt > 0 && wsum > 0.0) ? (float)((double)cnt / wsum) : 1.f;
     DMRG_CHECK_CUDA(cudaMemcpyAsync(flag + take, pos.data(), take * sizeof(int), cudaMemcpyHostToDevice, st));
-    compact_kernel<<<blocks, NT, 0, st>>>(flag + take, flag, take, xs, ys, m.d_x, m.d_y);
+    compact_kernel<<<blocks, NT, 0, st>>>(flag + take, flag, take, xs, ys, ws, wscale, m.d_x, m.d_y, m.d_wt);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
     cudaFree(flag);
@@ -422,12 +442,25 @@ int64_t mlp_collect(Mlp& m, const double* hd, const double* r, const double* t, 
 // Training entry used by the C-ABI: epochs over the set in batches of B rows
 // drawn by the counter-based generator; returns the first and last batch losses.
 void mlp_train(Mlp& m, int steps, int64_t B, float lr, uint64_t seed, float* loss_first, float* loss_last,
-               cudaStream_t st) {
+               float* held_first, float* held_last, cudaStream_t st) {
     DMRG_REQUIRE(m.n_set > 0, DMRG_EINVAL, "no training pairs collected");
     DMRG_REQUIRE(m.d_w, DMRG_EINVAL, "MLP not initialised");
     float* d_loss = m.d_grad + kMlpParams;
+    // the last tenth of the set (the latest solves) is held out of training
+    const int64_t n_hold = m.n_set >= 20 ? m.n_set / 10 : 0;
+    const int64_t n_train = m.n_set - n_hold;
+    auto held = [&](float* out) {
+        if (!out) return;
+        *out = 0.f;
+        if (n_hold == 0) return;
+        gradient_batch(m, m.d_x + n_train * kMlpIn, m.d_y + n_train, m.d_wt + n_train, n_hold, n_hold, 0, m.d_grad,
+                       d_loss, st);
+        DMRG_CHECK_CUDA(cudaMemcpyAsync(out, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
+    };
+    held(held_first);
     for (int s = 0; s < steps; ++s) {
-        gradient_batch(m, m.d_x, m.d_y, m.n_set, B, mix64_host(seed + 1 + (uint64_t)s), m.d_grad, d_loss, st);
+        gradient_batch(m, m.d_x, m.d_y, m.d_wt, n_train, B, mix64_host(seed + 1 + (uint64_t)s), m.d_grad, d_loss, st);
         if (s == 0 || s == steps - 1) {
             float l = 0.f;
             DMRG_CHECK_CUDA(cudaMemcpyAsync(&l, d_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -437,6 +470,7 @@ void mlp_train(Mlp& m, int steps, int64_t B, float lr, uint64_t seed, float* los
         }
         mlp_adam(m, lr, st);
     }
+    held(held_last);
     mlp_publish(m, st);
     DMRG_CHECK_CUDA(cudaStreamSynchronize(st));
     m.trained = true;

@@ -7,18 +7,17 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication", Numer. Algorithms 59, 2012):
 //
-//  * every 64-deep K stage of a 128 x 64 output tile is converted by loader
+//  * every 32-deep K stage of a 128 x 64 output tile is converted by loader
 //    warps: row r of A and column c of B get a power-of-two scale 2^E from the
-//    largest magnitude in their 64 elements, the element is rounded to a
+//    largest magnitude in their 32 elements, the element is rounded to a
 //    48-bit integer Q = round(|x| 2^(48-E)), and Q is cut into six 8-bit
 //    slices q_0..q_5 (q_0 <= 256) stored as bf16 (exact: at most 9 significant
 //    bits), so that x = sign * sum_i q_i 2^(E - 8(i+1)) up to 2^(E-49);
 //  * the slice products with i + j = g <= 5 are issued as tcgen05.mma
 //    (M = 128, N = 64, K = 16 per instruction) into one FP32 accumulator per
 //    order g in tensor memory.  Every product is an integer below 2^16 and
-//    each order's sum over the 64-deep stage stays below 2^24 for g <= 3, so
-//    those accumulations are exact whatever the order of the additions; orders
-//    4 and 5 (weights 2^-32, 2^-40 of order 0) may round in their last bit;
+//    each order's sum over the 32-deep stage stays below 2^24 for g <= 5, so
+//    the accumulations are exact whatever the order of the additions;
 //  * the epilogue warps read the six orders, combine them with the row and
 //    column scales and the segment's alpha into a double-float (two FP32)
 //    accumulator per element (FP32 arithmetic only: GB300's FP32 rate is ~64x
@@ -43,13 +42,14 @@ namespace {
 
 using namespace ptx;
 
-constexpr int OTM = 128, OTN = 64, OTK = 64;
+constexpr int OTM = 128, OTN = 64, OTK = 32;   // tile rows, columns, stage depth
+constexpr int ROWK = 64;                       // K of a swizzled slice row (two stages)
 constexpr int NSL = 6;                         // slices per operand
 constexpr int NORD = 6;                        // accumulated orders g = i + j = 0..5
-constexpr int A_SLICE = OTM * OTK * 2;         // 16 KB
-constexpr int B_SLICE = OTN * OTK * 2;         // 8 KB
+constexpr int A_SLICE = OTM * ROWK * 2;        // 16 KB
+constexpr int B_SLICE = OTN * ROWK * 2;        // 8 KB
 constexpr int SLICE_BYTES = NSL * (A_SLICE + B_SLICE);
-constexpr int EXP_SLOTS = 3;
+constexpr int EXP_SLOTS = 4;
 constexpr uint32_t TMEM_COLS = 512;            // 6 orders x 64 columns, rounded to a power of two
 // warps 0-7 epilogue (warp w: tile rows 32 (w % 4) .., columns 32 (w / 4) ..),
 // warps 8-11 loaders, warp 12 lane 0 MMA issuer; 13 warps keep 4 per SM
@@ -72,8 +72,8 @@ struct OzStage {
 constexpr int ACL_BYTES = NEPI * 32 * EPI_COLS * 4;
 constexpr int OZ_SMEM = 1024 + SLICE_BYTES + EXP_SLOTS * (int)sizeof(OzStage) + ACL_BYTES;
 
-// biased exponent field of x (0 for zero and subnormals)
-__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+// biased exponent field of a double from its high 32-bit word (0 for zero and subnormals)
+__device__ __forceinline__ int exp_field_hi(int hi) { return (hi >> 20) & 0x7FF; }
 
 // 48-bit integer magnitude of |x| 2^(48-E) (rounded half up), with E = ebias - 1023
 __device__ __forceinline__ uint64_t q48(double x, int ebias) {
@@ -92,15 +92,15 @@ __device__ __forceinline__ uint32_t bf16_of_int(uint32_t q, uint32_t sign) {
     return (__float_as_uint(f) >> 16) | (sign << 15);
 }
 
-// Convert N values (K indices KFIRST .. KFIRST+N-1 of one row of A or one
-// column of B, read by ld(kk) for kk = 0..N-1) into the six slices at
-// dst + s * slice_bytes, row `row` of a 128B-swizzled K-major tile.
-template <int N, int KFIRST, class Ld>
-__device__ __forceinline__ void store_slices(const Ld& ld, int ebias, uint32_t dst, int slice_bytes, int row) {
+// Convert N values (read by ld(kk), kk = 0..N-1) into the six slices at
+// dst + s * slice_bytes: row `row` of a 128B-swizzled K-major tile, 16-byte
+// chunks cbase .. cbase + N/8 - 1 of the row.
+template <int N, class Ld>
+__device__ __forceinline__ void store_slices(const Ld& ld, int ebias, uint32_t dst, int slice_bytes, int row,
+                                             int cbase) {
     const uint32_t rowoff = (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
-#pragma unroll 1
+#pragma unroll
     for (int cl = 0; cl < N / 8; ++cl) {
-        const int c = KFIRST / 8 + cl;  // 16-byte chunk along K
         uint32_t w[NSL][4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -121,6 +121,7 @@ __device__ __forceinline__ void store_slices(const Ld& ld, int ebias, uint32_t d
 #pragma unroll
             for (int s = 0; s < NSL; ++s) w[s][p] = b16[0][s] | (b16[1][s] << 16);
         }
+        const int c = cbase + cl;
         const uint32_t off = rowoff + (uint32_t)(((c ^ (row & 7)) & 7) << 4);
 #pragma unroll
         for (int s = 0; s < NSL; ++s)
@@ -145,17 +146,23 @@ __device__ __forceinline__ float pow2f(int k) {
     return __uint_as_float((uint32_t)(k + 127) << 23);
 }
 
+__device__ __forceinline__ int tile_nst(const Tile& T, const Seg* __restrict__ segs) {
+    int nst = 0;
+    for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + OTK - 1) / OTK;
+    return nst;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const Tile* __restrict__ tiles, int ntiles, int nvec, const Seg* __restrict__ segs, BufTable bt,
                    int* err) {
     extern __shared__ uint8_t smem_raw[];
-    // full: loaders -> MMA (slices and stage record written); stage: MMA -> epilogue
-    // (stage record visible, arrived after the previous accumulators were read);
-    // mma: MMA completion -> loaders (slice buffer free) and epilogue (orders
-    // ready); free: epilogue -> MMA (accumulators read)
-    __shared__ __align__(8) uint64_t full_bar, stage_bar, mma_bar, free_bar, drain_bar;
+    // full[h]: loaders -> MMA (slices of K half h and the stage record written);
+    // stage: MMA -> epilogue (stage record visible; arrived after the previous
+    // accumulators were read); mma[h]: MMA completion -> loaders (half h free)
+    // and epilogue (orders ready); free: epilogue -> MMA (accumulators read)
+    __shared__ __align__(8) uint64_t full_bar[2], mma_bar[2], stage_bar, free_bar, drain_bar;
     __shared__ uint32_t tmem_base_s;
-    __shared__ int32_t ebp[2][OTN];  // per-half column exponent fields of B (loaders)
+    __shared__ int32_t ebp[2][OTN];  // per-part column exponent fields of B (loaders)
     __shared__ int32_t load_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -165,9 +172,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
     if (warp == 0) tmem_alloc(smem_u32(&tmem_base_s), TMEM_COLS);
     if (tid == 0) {
-        mbar_init(smem_u32(&full_bar), NLOAD);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(smem_u32(&full_bar[h]), NLOAD);
+            mbar_init(smem_u32(&mma_bar[h]), 1);
+        }
         mbar_init(smem_u32(&stage_bar), 1);
-        mbar_init(smem_u32(&mma_bar), 1);
         mbar_init(smem_u32(&free_bar), NEPI);
         mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -183,10 +192,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         // ---------------- loaders / converters ----------------
         const int t = tid - NEPI * 32;
         uint32_t q = 0;
-        // the slice buffer is free once the previous stage's MMAs completed; one
-        // thread waits and the decision is shared, so the loaders stay uniform
+        // K half (q & 1) of the slices is free once the MMAs of stage q - 2
+        // completed; one thread waits and the decision is shared, so the loaders
+        // stay uniform
         auto begin = [&]() -> bool {
-            if (t == 0) load_ok = (q < 1 || mbar_wait(smem_u32(&mma_bar), (q - 1) & 1u)) ? 1 : 0;
+            if (t == 0)
+                load_ok = (q < 2 || mbar_wait(smem_u32(&mma_bar[q & 1u]), ((q >> 1) - 1) & 1u)) ? 1 : 0;
             loaders_sync();
             const bool ok = load_ok != 0;
             loaders_sync();
@@ -195,8 +206,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
             const Tile T = tiles[it % ntiles];
             const int v = it / ntiles;
-            int nst = 0;
-            for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + OTK - 1) / OTK;
+            const int nst = tile_nst(T, segs);
             int done = 0;
             if (nst == 0) {
                 if (!begin()) { failed = true; break; }
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     S.ah = S.al = 0.f;
                 }
                 fence_proxy_async();
-                mbar_arrive(smem_u32(&full_bar));
+                mbar_arrive(smem_u32(&full_bar[q & 1u]));
                 ++q;
                 continue;
             }
@@ -217,47 +227,47 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 for (int k0 = 0; k0 < Sg.k; k0 += OTK) {
                     if (!begin()) { failed = true; break; }
                     OzStage& S = stages[q % EXP_SLOTS];
-                    // A: thread t converts row m0 + t over k0 .. k0+63 (a first pass
-                    // finds the row's scale, the second reads the values again, from L1)
+                    const int cbase = (int)(q & 1u) * (OTK / 8);
+                    // A: thread t converts row m0 + t over k0 .. k0+31: the row's scale
+                    // from the high words (32 loads in flight), then the values
                     {
                         const int gi = T.m0 + t;
                         const bool rv = gi < T.m;
-                        auto lda = [&](int kk) -> double {
+                        const int kn = rv ? min(OTK, Sg.k - k0) : 0;
+                        auto idx = [&](int kk) -> int64_t {
                             const int k = k0 + kk;
-                            if (!rv || k >= Sg.k) return 0.0;
-                            return Sg.a_tr ? A[(int64_t)k * Sg.lda + gi] : A[(int64_t)gi * Sg.lda + k];
+                            return Sg.a_tr ? (int64_t)k * Sg.lda + gi : (int64_t)gi * Sg.lda + k;
                         };
                         int emax = 0;
-#pragma unroll 8
-                        for (int kk = 0; kk < 64; ++kk) emax = max(emax, exp_field(lda(kk)));
+#pragma unroll
+                        for (int kk = 0; kk < OTK; ++kk)
+                            if (kk < kn) emax = max(emax, exp_field_hi(reinterpret_cast<const int*>(A + idx(kk))[1]));
                         const int ebias = emax + 1;  // |x| < 2^(ebias - 1023)
                         S.ea[t] = emax ? ebias - 1023 : -1000;
-                        store_slices<64, 0>(lda, ebias, sA, A_SLICE, t);
+                        auto lda = [&](int kk) -> double { return kk < kn ? A[idx(kk)] : 0.0; };
+                        store_slices<OTK>(lda, ebias, sA, A_SLICE, t, cbase);
                     }
-                    // B: thread t converts column (t & 63) over the K half (t >> 6)
+                    // B: threads t and t + 64 convert column (t & 63), K parts of 16
                     {
-                        const int c = t & 63, half = t >> 6;
+                        const int c = t & 63, part = t >> 6;
                         const int gj = T.n0 + c;
-                        const bool cv = gj < T.n;
-                        const int kb = k0 + 32 * half;
-                        auto ldb = [&](int kk) -> double {
+                        const int kb = k0 + 16 * part;
+                        const int kn = gj < T.n ? max(0, min(16, Sg.k - kb)) : 0;
+                        auto idx = [&](int kk) -> int64_t {
                             const int k = kb + kk;
-                            if (!cv || k >= Sg.k) return 0.0;
-                            return Sg.b_tr ? B[(int64_t)gj * Sg.ldb + k] : B[(int64_t)k * Sg.ldb + gj];
+                            return Sg.b_tr ? (int64_t)gj * Sg.ldb + k : (int64_t)k * Sg.ldb + gj;
                         };
                         int emax = 0;
-#pragma unroll 8
-                        for (int kk = 0; kk < 32; ++kk) emax = max(emax, exp_field(ldb(kk)));
-                        ebp[half][c] = emax;
+#pragma unroll
+                        for (int kk = 0; kk < 16; ++kk)
+                            if (kk < kn) emax = max(emax, exp_field_hi(reinterpret_cast<const int*>(B + idx(kk))[1]));
+                        ebp[part][c] = emax;
                         loaders_sync();
                         emax = max(ebp[0][c], ebp[1][c]);
                         const int ebias = emax + 1;
-                        if (half == 0) {
-                            S.eb[c] = emax ? ebias - 1023 : -1000;
-                            store_slices<32, 0>(ldb, ebias, sB, B_SLICE, c);
-                        } else {
-                            store_slices<32, 32>(ldb, ebias, sB, B_SLICE, c);
-                        }
+                        if (part == 0) S.eb[c] = emax ? ebias - 1023 : -1000;
+                        auto ldb = [&](int kk) -> double { return kk < kn ? B[idx(kk)] : 0.0; };
+                        store_slices<16>(ldb, ebias, sB, B_SLICE, c, cbase + 2 * part);
                     }
                     if (t == 0) {
                         const float ah = (float)Sg.alpha;
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         S.flags = (done == 0 ? 1 : 0) | (done == nst - 1 ? 2 : 0);
                     }
                     fence_proxy_async();
-                    mbar_arrive(smem_u32(&full_bar));
+                    mbar_arrive(smem_u32(&full_bar[q & 1u]));
                     ++q;
                     ++done;
                 }
@@ -279,11 +289,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t id = idesc_mn(0, 0, 0, OTN, OTM);
             for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
                 const Tile T = tiles[it % ntiles];
-                int nst = 0;
-                for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + OTK - 1) / OTK;
+                int nst = tile_nst(T, segs);
                 if (nst == 0) nst = 1;
                 for (int st = 0; st < nst; ++st, ++q) {
-                    if (!mbar_wait(smem_u32(&full_bar), q & 1u)) { failed = true; break; }
+                    const uint32_t h = q & 1u;
+                    if (!mbar_wait(smem_u32(&full_bar[h]), (q >> 1) & 1u)) { failed = true; break; }
                     if (q >= 1 && !mbar_wait(smem_u32(&free_bar), (q - 1) & 1u)) { failed = true; break; }
                     mbar_arrive(smem_u32(&stage_bar));
                     tc_fence_after();
@@ -297,14 +307,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                                 const int j = g - i;
 #pragma unroll
                                 for (int kk = 0; kk < OTK / 16; ++kk) {
-                                    const uint64_t ad = sdesc(sA + i * A_SLICE + kk * 32, 16, 1024);
-                                    const uint64_t bd = sdesc(sB + j * B_SLICE + kk * 32, 16, 1024);
+                                    const uint32_t koff = (h * (OTK / 16) + kk) * 32;
+                                    const uint64_t ad = sdesc(sA + i * A_SLICE + koff, 16, 1024);
+                                    const uint64_t bd = sdesc(sB + j * B_SLICE + koff, 16, 1024);
                                     mma_bf16(dt, ad, bd, id, (i == 0 && kk == 0) ? 0u : 1u);
                                 }
                             }
                         }
                     }
-                    mma_commit(smem_u32(&mma_bar));
+                    mma_commit(smem_u32(&mma_bar[h]));
                 }
             }
             mma_commit(smem_u32(&drain_bar));
@@ -318,8 +329,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
             const Tile T = tiles[it % ntiles];
             const int v = it / ntiles;
-            int nst = 0;
-            for (int s = T.seg_beg; s < T.seg_end; ++s) nst += (segs[s].k + OTK - 1) / OTK;
+            int nst = tile_nst(T, segs);
             if (nst == 0) nst = 1;
             float ach[EPI_COLS];
             float* acl = acl_s + tid;  // acl[c * NEPI * 32]
@@ -331,7 +341,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int st = 0; st < nst; ++st, ++q) {
                 int ok = 1;
                 if (lane == 0)
-                    ok = (mbar_wait(smem_u32(&stage_bar), q & 1u) && mbar_wait(smem_u32(&mma_bar), q & 1u)) ? 1 : 0;
+                    ok = (mbar_wait(smem_u32(&stage_bar), q & 1u) &&
+                          mbar_wait(smem_u32(&mma_bar[q & 1u]), (q >> 1) & 1u))
+                             ? 1
+                             : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { failed = true; break; }
                 __syncwarp();
@@ -344,6 +357,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 }
                 const int er = S.ea[row];
                 const float ah = S.ah, al = S.al;
+                const bool unit = (ah == 1.f || ah == -1.f) && al == 0.f;  // alpha = +-1: a sign only
                 const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chalf * EPI_COLS);
 #pragma unroll
                 for (int cc = 0; cc < EPI_COLS / 4; ++cc) {
@@ -370,11 +384,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                         const float sc = pow2f(er + S.eb[chalf * EPI_COLS + c] - 16);
                         sh *= sc;
                         sl *= sc;
-                        // times alpha (double-float product)
-                        const float p = sh * ah;
-                        float pe = fmaf(sh, ah, -p);
-                        pe = fmaf(sh, al, pe);
-                        pe = fmaf(sl, ah, pe);
+                        float p, pe;
+                        if (unit) {
+                            p = sh * ah;
+                            pe = sl * ah;
+                        } else {  // times alpha (double-float product)
+                            p = sh * ah;
+                            pe = fmaf(sh, ah, -p);
+                            pe = fmaf(sh, al, pe);
+                            pe = fmaf(sl, ah, pe);
+                        }
                         float nh;
                         two_sum(ach[c], p, nh, e);
                         ach[c] = nh;
@@ -412,6 +431,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
 int oz_tile_rows() { return OTM; }
 int oz_tile_cols() { return OTN; }
+int oz_stage_depth() { return OTK; }
 
 int* oz_error_word() {
     static int* d = nullptr;

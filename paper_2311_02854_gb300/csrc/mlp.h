@@ -32,6 +32,7 @@ struct Mlp {
     // training set: features (n x 5) and targets (n), FP32, on the device
     float* d_x = nullptr;
     float* d_y = nullptr;
+    float* d_wt = nullptr;  // pair weights (r_i / (H_ii - theta))^2, mean 1 per solve
     int64_t n_set = 0, cap_set = 0;
     // training workspace (per batch): activations and their gradients
     float* d_work = nullptr;
@@ -50,9 +51,11 @@ void mlp_features(const Mlp& m, const double* hd, const double* r, double theta,
                   float* x, cudaStream_t st);
 // g = MLP(x) for n feature rows; bf16 = 1 uses the bf16 weights
 void mlp_forward(const Mlp& m, const float* x, int64_t n, float* g, bool bf16, cudaStream_t st);
-// gradient of the mean squared error (1/n) sum (g(x_i) - y_i)^2 with respect to
-// the parameters into grad (kMlpParams) and the loss into *loss (device)
-void mlp_gradient(Mlp& m, const float* x, const float* y, int64_t n, float* grad, float* loss, cudaStream_t st);
+// gradient of the weighted mean squared error (1/n) sum w_i (g(x_i) - y_i)^2
+// (w = 1 when w is null) with respect to the parameters into grad (kMlpParams)
+// and the loss into *loss (device)
+void mlp_gradient(Mlp& m, const float* x, const float* y, const float* w, int64_t n, float* grad, float* loss,
+                  cudaStream_t st);
 // one Adam step on the parameters with the gradient in m.d_grad
 void mlp_adam(Mlp& m, float lr, cudaStream_t st);
 // bf16 copy of the parameters for inference
@@ -69,9 +72,10 @@ int64_t mlp_collect(Mlp& m, const double* hd, const double* r, const double* t, 
 double dev_absmax(const double* x, double shift, int64_t n, double* work, cudaStream_t st);
 
 // steps Adam steps on batches of B pairs drawn (counter-based, seeded) from the
-// training set; loss of the first and last batch to the host; publishes the
-// bf16 weights and marks the network trained
+// first nine tenths of the training set (weighted loss); loss of the first and
+// last batch, and of the held-out last tenth before and after, to the host;
+// publishes the bf16 weights and marks the network trained
 void mlp_train(Mlp& m, int steps, int64_t B, float lr, uint64_t seed, float* loss_first, float* loss_last,
-               cudaStream_t st);
+               float* held_first, float* held_last, cudaStream_t st);
 
 }  // namespace dmrg

@@ -572,6 +572,10 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
     cudaEventRecord(e0, st);
     const auto bl = P.mps.bonds[k - 1];
     const auto br = P.mps.bonds[k + 1];
+    // the bond's intermediates are not needed any more (the next bond forms its
+    // own); freeing them first lowers the peak of the renormalisation below
+    free_interms(P, P.interm);
+    P.bond = -1;  // no sigma at this bond any more (its intermediates are gone)
     // groups by the label of bond k
     std::map<QN, Group> groups;
     for (const Plan::Sector& s : P.layout) {
@@ -907,7 +911,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
         for (auto& b : br) maxd = std::max(maxd, b[2]);
         ensure_ident(P, maxd);
         P.f64_tiles(pl);
-        pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), 1 << 14);
+        pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap_f64(P), 1 << 14);
         ensure_scratch_f64(P, std::max<int64_t>(pl.scratch_elems, 1) * nr);
         pl.upload(st);
         DMRG_CHECK_CUDA(cudaMemsetAsync(next_psi, 0, (size_t)nr * ndim * 8, st));

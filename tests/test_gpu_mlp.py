@@ -1,6 +1,7 @@
-"""Learned Davidson preconditioner on the GPU: forward and gradient kernels
-against the oracle's FP64 network, training on harvested Jacobi-Davidson pairs,
-and Davidson with the trained network against the plain (Jacobi) method."""
+"""Learned Davidson preconditioner on the GPU: forward and (weighted) gradient
+kernels against the oracle's FP64 network, weighted training on harvested
+Jacobi-Davidson pairs with a held-out set, and Davidson with the trained
+network against the plain (Jacobi) method at three bonds."""
 import numpy as np
 import pytest
 
@@ -45,46 +46,70 @@ def test_forward_and_gradient_match_oracle(tmp_path):
     grad = dgrad.cpu().numpy()
     assert abs(float(dloss.item()) - L_ref) <= 1e-5 * L_ref
     assert np.max(np.abs(grad - grad_ref)) <= 1e-4 * (1e-3 + np.max(np.abs(grad_ref)))
+    # the weighted loss of the training (weights of the harvested pairs)
+    w = rng.uniform(0.0, 4.0, 1000).astype(np.float32)
+    Lw_ref, gradw_ref = omlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), y.astype(np.float64),
+                                           w.astype(np.float64))
+    plan.mlp_gradient(dX, dy, dgrad, dloss, w=torch.from_numpy(w).cuda())
+    gradw = dgrad.cpu().numpy()
+    assert abs(float(dloss.item()) - Lw_ref) <= 1e-5 * Lw_ref
+    assert np.max(np.abs(gradw - gradw_ref)) <= 1e-4 * (1e-3 + np.max(np.abs(gradw_ref)))
     plan.close()
 
 
-def test_training_on_harvested_pairs_reduces_the_loss(tmp_path):
+def test_training_on_harvested_pairs_reduces_the_held_out_loss(tmp_path):
+    """Weighted training on harvested Jacobi-Davidson pairs lowers the loss of
+    pairs held out of training (the last tenth of the set)."""
     torch = cuda_torch()
     plan, *_ = _plan(tmp_path)
     plan.mlp_init(3)
-    x = torch.from_numpy(si.random_vector(plan.dim, seed=1)).cuda()
-    e, n_pairs = plan.mlp_harvest(x, max_iter=12, jd_iters=60, per_solve=4096)
-    print(f"harvest: E = {e:.10f}, {n_pairs} pairs")
-    assert n_pairs > 1000
-    l0, l1 = plan.mlp_train(steps=300, batch=2048, lr=3e-3, seed=11)
-    print(f"training loss {l0:.4e} -> {l1:.4e}")
-    # the per-element targets are noisy functions of the five inputs: the network
-    # can only learn their conditional mean, so the loss falls but not to zero
-    assert np.isfinite(l1) and l1 < l0
+    for seed in (1, 2):
+        x = torch.from_numpy(si.random_vector(plan.dim, seed=seed)).cuda()
+        e, n_pairs = plan.mlp_harvest(x, max_iter=12, jd_iters=60, per_solve=4096)
+        assert n_pairs > 1000
+    l0, l1, h0, h1 = plan.mlp_train(steps=400, batch=2048, lr=3e-3, seed=11, held_out=True)
+    print(f"training loss {l0:.4e} -> {l1:.4e}, held-out {h0:.4e} -> {h1:.4e}")
+    assert np.isfinite(l1) and np.isfinite(h1)
+    assert h1 < h0
     plan.close()
 
 
 def test_trained_preconditioner_against_jacobi(tmp_path):
-    """Same bond, same guess: Davidson with the trained g against plain Jacobi.
-    Both reach the oracle eigenvalue; the iteration counts are reported."""
+    """Pairs harvested at bond 5 of K=10 (three plain runs from other guesses),
+    weighted training, then Davidson with the trained g against plain Jacobi at
+    three bonds (4, 5, 6; same guess each), FP64: both reach the same energy;
+    the iteration counts to |r| <= 1e-6 are reported (the measured ratio is
+    recorded with the design notes)."""
     torch = cuda_torch()
-    K, N, D, k = 10, 10, 128, 5
-    plan, h, L, mps = _plan(tmp_path, K=K, N=N, D=D, k=k)
-    ts = Oracle(h, eri_from_cholesky(L), N, 0, mps).two_site(k)
-    guess = si.random_vector(ts.dim, seed=1)
-    th_ref, _, _ = davidson(ts.sigma, ts.hdiag(), guess[None], 1, 1e-10, 400)
+    g = gpu_lib()
+    K, N, D = 10, 10, 128
+    plan, h, L, mps = _plan(tmp_path, K=K, N=N, D=D, k=5)
     plan.mlp_init(3)
     for seed in (21, 22, 23):  # pairs from plain runs started at other guesses
-        x = torch.from_numpy(si.random_vector(ts.dim, seed=seed)).cuda()
+        x = torch.from_numpy(si.random_vector(plan.dim, seed=seed)).cuda()
         plan.mlp_harvest(x, max_iter=15, jd_iters=60, per_solve=8192)
-    l0, l1 = plan.mlp_train(steps=600, batch=4096, lr=3e-3, seed=7)
-    res = {}
-    for name, pc in (("jacobi", 0), ("mlp", 1)):
-        x = torch.from_numpy(guess.copy()).cuda()
-        e, it, conv = plan.davidson(x, 1, tol=1e-6, max_iter=300, precond=pc)
-        res[name] = (e[0], it)
-        assert abs(e[0] - th_ref[0]) < 1e-8
-    st = plan.stats()
-    print(f"loss {l0:.3e} -> {l1:.3e}; Davidson iterations to |r| <= 1e-6: jacobi {res['jacobi'][1]}, "
-          f"mlp {res['mlp'][1]}; fallbacks {st['precond_fallbacks']}")
+    l0, l1, h0, h1 = plan.mlp_train(steps=600, batch=4096, lr=3e-3, seed=7, held_out=True)
+    params = plan.mlp_params()
     plan.close()
+    its = {"jacobi": [], "mlp": []}
+    for k in (4, 5, 6):
+        h2, L2, mps2, path2 = make_case(tmp_path, K, N, 0, D, center=k)
+        p2 = g.Plan(h2, L2, K, N, 0, D, path2)
+        p2.set_bond(k)
+        p2.mlp_params(params)
+        guess = si.random_vector(p2.dim, seed=1)
+        en = {}
+        for name, pc in (("jacobi", 0), ("mlp", 1)):
+            x = torch.from_numpy(guess.copy()).cuda()
+            e, it, conv = p2.davidson(x, 1, tol=1e-6, max_iter=400, precond=pc)
+            assert conv
+            en[name] = e[0]
+            its[name].append(it)
+        assert abs(en["mlp"] - en["jacobi"]) < 1e-8
+        st = p2.stats()
+        assert st["precond_fallbacks"] == 0
+        p2.close()
+    ratio = sum(its["mlp"]) / sum(its["jacobi"])
+    print(f"loss {l0:.3e} -> {l1:.3e}, held-out {h0:.3e} -> {h1:.3e}; Davidson iterations to |r| <= 1e-6 at "
+          f"bonds 4, 5, 6: jacobi {its['jacobi']}, mlp {its['mlp']} (ratio {ratio:.3f})")
+    assert h1 < h0

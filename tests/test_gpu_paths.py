@@ -226,3 +226,42 @@ def test_refined_two_roots_and_state_averaged_decimation(tmp_path):
     np.testing.assert_allclose(gv @ gv.T, gr @ gr.T, atol=1e-10)
     np.testing.assert_allclose(gv @ hg.T, gr @ hr.T, atol=1e-9)
     plan.close()
+
+
+def test_bond_update_from_host_buffers_matches_device_calls(tmp_path):
+    """dmrg_update_bond_host (guess in and next guess out through host memory)
+    against dmrg_davidson + dmrg_decimate on device buffers, from the same guess:
+    same energy, discarded weight and next-bond guess (FP64)."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    K, N, twoS, D, k, Dcut = 8, 8, 0, 64, 4, 20
+    h, L, mps, path = make_case(tmp_path, K, N, twoS, D, center=k)
+    guess = si.random_vector(make_dim(g, h, L, K, N, twoS, D, path, k), seed=3)
+    res = []
+    for host in (False, True):
+        plan = g.Plan(h, L, K, N, twoS, D, path, tol=1e-9, max_iter=300)
+        plan.set_bond(k)
+        cap = 4 * plan.dim
+        if host:
+            nxt = np.zeros(cap)
+            e, it, w, nd, conv = plan.update_bond_host(guess.copy(), 1, Dcut, True, next_psi=nxt)
+            res.append((e[0], w, nxt[:nd].copy()))
+        else:
+            x = torch.from_numpy(guess.copy()).cuda()
+            e, it, conv = plan.davidson(x, 1, tol=1e-9, max_iter=300)
+            dn = torch.zeros(cap, dtype=torch.float64, device="cuda")
+            w, nd = plan.decimate(x, 1, Dcut, True, next_psi=dn, next_cap=cap)
+            res.append((e[0], w, dn[:nd].cpu().numpy()))
+        assert conv
+        plan.close()
+    (e0, w0, g0), (e1, w1, g1) = res
+    assert abs(e0 - e1) < 1e-10 and abs(w0 - w1) < 1e-14
+    assert g0.shape == g1.shape and np.allclose(g0, g1, rtol=0, atol=1e-10)
+
+
+def make_dim(g, h, L, K, N, twoS, D, path, k):
+    plan = g.Plan(h, L, K, N, twoS, D, path)
+    plan.set_bond(k)
+    d = plan.dim
+    plan.close()
+    return d

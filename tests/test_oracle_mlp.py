@@ -67,3 +67,30 @@ def test_planted_error_in_the_backward_pass_is_caught():
     tm[i] -= h
     fd = (mlp.loss_and_grad(tp, X, y)[0] - mlp.loss_and_grad(tm, X, y)[0]) / (2 * h)
     assert abs(fd - grad[i]) < 1e-6 < abs(fd - wrong[i])
+
+
+def test_weighted_gradient_matches_central_differences():
+    """The weighted loss mean(w (g - y)^2) of the learned preconditioner's
+    training: its gradient against central differences, and two special cases
+    (equal weights scale the plain loss; a weight vector that selects one pair
+    gives that pair's loss times n)."""
+    rng = np.random.default_rng(4)
+    theta = _theta(rng)
+    X = rng.standard_normal((40, 5))
+    y = rng.standard_normal(40)
+    w = rng.uniform(0.0, 5.0, 40)
+    L, grad = mlp.loss_and_grad(theta, X, y, w)
+    h = 1e-6
+    for i in np.concatenate([rng.choice(mlp.N_PARAMS, 40, replace=False), [0, 4479, 4608]]):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss_and_grad(tp, X, y, w)[0] - mlp.loss_and_grad(tm, X, y, w)[0]) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-7 + 1e-6 * abs(fd), (i, fd, grad[i])
+    L1, g1 = mlp.loss_and_grad(theta, X, y)
+    L3, g3 = mlp.loss_and_grad(theta, X, y, np.full(40, 3.0))
+    assert abs(L3 - 3 * L1) <= 1e-12 * L3 and np.allclose(g3, 3 * g1, rtol=1e-12, atol=1e-15)
+    sel = np.zeros(40)
+    sel[7] = 1.0
+    g7, _, _ = mlp.forward(theta, X[7:8])
+    assert abs(mlp.loss_and_grad(theta, X, y, sel)[0] * 40 - (g7[0] - y[7]) ** 2) <= 1e-12
