@@ -555,6 +555,46 @@ def run_mlp_study(args):
                       "ratio_mlp_over_jacobi": im / max(ij, 1)}), flush=True)
 
 
+def run_sweep_probe(args):
+    """--sweep: D-ramped sweeps of the whole chain (the bond dimension of sweep i
+    is --sweep-d[i]) from a seeded MPS of bond dimension --sweep-d[0] centred on
+    the first bond, with the host tier on (--host-tier): per sweep the wall time,
+    seconds per site = wall / 2(K-1), energy, discarded weight, Davidson
+    iterations and the per-phase device / host times from the library's
+    counters.  Prints one JSON line per sweep (not the benchmark contract line)."""
+    import torch
+    import paper_2311_02854_gb300 as g
+
+    w = dict(WORKLOADS[args.workload])
+    K = w["K"]
+    ds = [int(x) for x in args.sweep_d.split(",")]
+    w["D"] = ds[0]
+    td = tempfile.mkdtemp(prefix="dmrg_sweep_")
+    h, L, bonds, path = make_inputs(w, td, 1)
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], ds[-1], path, precision=PRECISIONS[args.precision],
+                  tol=args.tol, max_iter=args.dav_iters, host_tier=int(args.host_tier),
+                  fp64_store=int(args.fp64_store), fp64_tc=int(args.fp64_tc), refine=int(args.refine))
+    keys = ("ms_davidson", "ms_decim", "ms_renorm", "ms_interm", "ms_sigma_dev", "ms_host_plan", "ms_hdiag",
+            "ms_tier_wait", "tier_out_bytes", "tier_in_bytes", "sigma_calls")
+    prev = plan.stats()
+    for i, D in enumerate(ds):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        e, wd = plan.sweep(1, [D])
+        torch.cuda.synchronize()
+        wall = time.time() - t0
+        st = plan.stats()
+        print(json.dumps({"mode": "sweep", "workload": args.workload, "precision": args.precision,
+                          "sweep": i, "D": D, "wall_s": round(wall, 2),
+                          "s_per_site": round(wall / (2 * (K - 1)), 3), "energy": float(e[0]),
+                          "discarded_max": float(wd[0]),
+                          "delta": {k: (st[k] - prev[k]) for k in keys},
+                          "device_bytes_peak": st["device_bytes_peak"], "host_bytes": st["host_bytes"]}),
+              flush=True)
+        prev = st
+    plan.close()
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -611,6 +651,10 @@ def main():
     ap.add_argument("--mlp-per-solve", type=int, default=16384)
     ap.add_argument("--mlp-steps", type=int, default=2000)
     ap.add_argument("--mlp-eval-precision", default="fp64tc", choices=sorted(PRECISIONS))
+    ap.add_argument("--sweep", action="store_true",
+                    help="D-ramped sweeps of the whole chain with the host tier; s/site per sweep")
+    ap.add_argument("--sweep-d", default="500,1000,2000,3000", help="--sweep: bond dimension of each sweep")
+    ap.add_argument("--host-tier", type=int, default=1, help="--sweep: environment blocks in pinned host memory")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -618,6 +662,8 @@ def main():
         run_sigma_probe(args)
     elif args.mlp_study:
         run_mlp_study(args)
+    elif args.sweep:
+        run_sweep_probe(args)
     else:
         run_mine(args)
 

@@ -69,10 +69,10 @@ typedef enum {
  * BF16X6: three pieces x = hi + lo + lo2 (24 significant bits, FP32-like
  *   storage) and the six products whose piece orders sum to at most 2.
  * FP64_TC: FP64 operator store and results, every product FP64-accurate on the
- *   bf16 tensor cores (error-free splitting, Ozaki et al. 2012: per 64-deep K
+ *   bf16 tensor cores (error-free splitting, Ozaki et al. 2012: per 32-deep K
  *   stage each row of A and column of B is scaled by a power of two and cut
  *   into six 8-bit slices; the slice products whose orders sum to <= 5
- *   accumulate in FP32 tensor memory, exactly for the four leading orders;
+ *   accumulate exactly in FP32 tensor memory, one accumulator per order;
  *   the orders are combined in double-float arithmetic and written as FP64).
  *   Per product, the error is bounded by about 2^-45 times the row and column
  *   maxima times the depth; not bitwise FP64, no FP64 arithmetic units. */
@@ -134,6 +134,15 @@ typedef struct {
                                intermediates, dmrg_sigma_fp64, the residual correction and FP64
                                Rayleigh quotients) run on the FP64-accurate tensor-core engine of
                                DMRG_FP64_TC instead of FP64 arithmetic units; default 0 */
+    int host_tier;          /* dmrg_sweep (Sec. 2.3, the operators of blocks away from the
+                               current bond kept off the GPU): 1 = every environment block
+                               that the current and the next bond update do not read is kept
+                               in pinned host memory only.  A block is copied out once, on a
+                               copy stream, while the bond's Davidson runs (blocks never change
+                               after they are built); the next bond's block is copied back on
+                               the same stream, and the compute stream waits for it where it is
+                               first used.  Results are bitwise those of host_tier = 0.  A failed
+                               pinned allocation returns DMRG_ENOMEM; default 0 */
 } dmrg_options;
 
 typedef struct {
@@ -194,6 +203,11 @@ typedef struct {
                                      FP64 Rayleigh quotients), all vectors */
     double ms_sigma_acc;          /* their device time */
     double sigma_acc_flops;       /* their algorithmic FLOPs */
+    int64_t device_bytes_peak;    /* largest device_bytes since the plan was made */
+    int64_t host_bytes;           /* pinned host memory held by the host tier */
+    int64_t tier_out_bytes;       /* bytes copied device -> host by the host tier */
+    int64_t tier_in_bytes;        /* bytes copied host -> device by the host tier */
+    double ms_tier_wait;          /* host time spent waiting for host-tier copies to finish */
 } dmrg_stats_t;
 
 /* Default options: FP64, 1 root, tol 1e-6, 200 iterations, Jacobi. */

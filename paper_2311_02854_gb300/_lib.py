@@ -27,7 +27,7 @@ class Options(C.Structure):
                 ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
                 ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int),
                 ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int), ("refine", C.c_int), ("max_refine", C.c_int),
-                ("fp64_tc", C.c_int)]
+                ("fp64_tc", C.c_int), ("host_tier", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -49,7 +49,9 @@ class Stats(C.Structure):
                 ("renorm_flops_total", C.c_double), ("interm_flops_total", C.c_double),
                 ("davidson_rnorm_last", C.c_double), ("davidson_conv_last", C.c_int),
                 ("davidson_stalled_last", C.c_int), ("davidson_refine_last", C.c_int), ("sigma_chunks", C.c_int),
-                ("sigma_acc_calls", C.c_int64), ("ms_sigma_acc", C.c_double), ("sigma_acc_flops", C.c_double)]
+                ("sigma_acc_calls", C.c_int64), ("ms_sigma_acc", C.c_double), ("sigma_acc_flops", C.c_double),
+                ("device_bytes_peak", C.c_int64), ("host_bytes", C.c_int64), ("tier_out_bytes", C.c_int64),
+                ("tier_in_bytes", C.c_int64), ("ms_tier_wait", C.c_double)]
 
     def as_dict(self):
         def conv(v):

@@ -280,6 +280,7 @@ SigmaShape tune_sigma_shape(Plan& P, int k, const ProductList& tl, int64_t cap, 
 
 void free_block(Plan& P, std::unique_ptr<Block>& b) {
     if (!b) return;
+    tier_release(P, *b);
     P.free(b->d, b->n);
     P.free_bf16(b->h, b->n);
     P.free_lo(b->l, b->n);
@@ -734,19 +735,33 @@ void ensure_env(Plan& P, int k) {
     const int m = k - 1;
     int have = m;
     while (have > 0 && !P.left[have]) --have;
-    // keep the block next to the new one (a step back needs it) and free the rest
+    // keep the block next to the new one (a step back needs it) and free the
+    // rest; sweeps keep them all, with the host tier off the device
+    const bool tier = P.opt.keep_envs && P.opt.host_tier;
     for (int j = have + 1; j <= m; ++j) {
+        tier_need(P, *P.left[j - 1]);
         P.left[j] = renormalise(P, *P.left[j - 1], j, true);
         if (!P.opt.keep_envs && j - 1 >= 1 && j - 1 < m - 1) free_block(P, P.left[j - 1]);
+        if (tier && j - 1 < m - 1) {
+            tier_out(P, *P.left[j - 1]);
+            tier_drain(P, false);
+        }
     }
     if (!P.right[K]) P.right[K] = make_vacuum(P, true);
     const int mr = k + 1;
     int haver = mr;
     while (haver < K && !P.right[haver]) ++haver;
     for (int j = haver - 1; j >= mr; --j) {
+        tier_need(P, *P.right[j + 1]);
         P.right[j] = renormalise(P, *P.right[j + 1], j + 1, false);
         if (!P.opt.keep_envs && j + 1 <= K - 1 && j + 1 > mr + 1) free_block(P, P.right[j + 1]);
+        if (tier && j + 1 > mr + 1) {
+            tier_out(P, *P.right[j + 1]);
+            tier_drain(P, false);
+        }
     }
+    tier_need(P, *P.left[m]);
+    tier_need(P, *P.right[mr]);
 }
 
 void build_layout(Plan& P, int k) {
@@ -778,6 +793,7 @@ void set_bond(Plan& P, int k) {
     DMRG_REQUIRE(k >= 1 && k <= P.K - 1, DMRG_EINVAL, "bond index out of range");
     DMRG_REQUIRE(k == P.mps.center, DMRG_EINVAL,
                  "bond " + std::to_string(k) + " is not the MPS centre " + std::to_string(P.mps.center));
+    if (P.opt.host_tier) tier_drain(P, true);  // evictions started at the previous bond
     ensure_env(P, k);
     const Block& L = *P.left[k - 1];
     const Block& R = *P.right[k + 1];

@@ -28,6 +28,18 @@ void sigma_fp64(Plan& P, const double* psi, double* out, int nvec, cudaStream_t 
 void sigma_fp64_units(Plan& P, const double* psi, double* out, int nvec, cudaStream_t st);
 void hdiag(Plan& P, double* out, cudaStream_t st);
 
+// tier.cu: environment blocks in pinned host memory between their uses
+void tier_out(Plan& P, Block& b);   // start the eviction of a resident block
+void tier_in(Plan& P, Block& b);    // start bringing an evicted block back (prefetch)
+void tier_need(Plan& P, Block& b);  // the block is used next on P.stream
+void tier_drain(Plan& P, bool wait);  // free the device arrays of evictions whose copies are done
+                                      // (wait: wait for every copy first)
+void tier_release(Plan& P, Block& b);  // before a block is freed
+void tier_destroy(Plan& P);
+// evict every block that the bond k update and the next bond do not use, and
+// prefetch the next bond's block (forward: right[k+2], backward: left[k-2])
+void tier_policy(Plan& P, int k, bool forward);
+
 // solver.cu
 dmrg_status davidson(Plan& P, double* psi, int n_roots, double tol, int max_iter, int precond,
                      double* energies, int* iters);

@@ -158,6 +158,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->refine = 0;
     o->max_refine = 0;
     o->fp64_tc = 0;
+    o->host_tier = 0;
 }
 
 const char* dmrg_version(void) {

@@ -25,11 +25,15 @@
 //    FP64 result.
 //
 // The work list is the FP64 engine's (Tile / Seg records over FP64 buffers of
-// a BufTable), lowered with 128-row tiles.  Persistent CTAs, one per SM, walk
-// the tiles round-robin; warps 0-3 epilogue (warp w owns tensor-memory lanes
-// and tile rows 32w..32w+31), warps 4-7 loaders, warp 8 lane 0 issues the MMAs.
-// One slice buffer: the loaders convert stage q+1 while the epilogue drains
-// stage q.  Every wait is bounded; a timeout sets the device error word.
+// a BufTable), lowered with 128 x 64 tiles and uploaded longest first.
+// Persistent CTAs, one per SM, walk (tile, vector) items with the vectors
+// innermost, so the CTAs that run at the same time share their operator tiles
+// in L2.  Slices are kept in 128B-swizzled rows 64 deep that hold two stages,
+// so stage q+1 is converted into the other half while the tensor cores consume
+// stage q.  Warps 0-7 epilogue (warp w: tile rows 32 (w % 4) .., columns
+// 32 (w / 4) ..), warps 8-11 loaders (A rows one per thread, B columns two
+// threads each), warp 12 lane 0 issues the MMAs.  Every wait is bounded; a
+// timeout sets the device error word.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -204,8 +208,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             return ok;
         };
         for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
-            const Tile T = tiles[it % ntiles];
-            const int v = it / ntiles;
+            const Tile T = tiles[it / nvec];
+            const int v = it % nvec;
             const int nst = tile_nst(T, segs);
             int done = 0;
             if (nst == 0) {
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             uint32_t q = 0;
             const uint32_t id = idesc_mn(0, 0, 0, OTN, OTM);
             for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
-                const Tile T = tiles[it % ntiles];
+                const Tile T = tiles[it / nvec];
                 int nst = tile_nst(T, segs);
                 if (nst == 0) nst = 1;
                 for (int st = 0; st < nst; ++st, ++q) {
@@ -327,8 +331,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int row = quarter * 32 + lane;
         uint32_t q = 0;
         for (int it = blockIdx.x; it < total && !failed; it += gridDim.x) {
-            const Tile T = tiles[it % ntiles];
-            const int v = it / ntiles;
+            const Tile T = tiles[it / nvec];
+            const int v = it % nvec;
             int nst = tile_nst(T, segs);
             if (nst == 0) nst = 1;
             float ach[EPI_COLS];

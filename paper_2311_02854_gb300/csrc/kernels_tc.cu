@@ -2,7 +2,10 @@
 // operands staged in shared memory (128B-swizzled canonical layouts, K-major
 // or MN-major), tcgen05.mma kind::f16 with bf16 inputs and FP32 accumulation
 // in tensor memory, completion tracked by mbarriers, persistent
-// warp-specialised CTAs (one per SM) walking the tiles round-robin.  One output
+// warp-specialised CTAs (one per SM) walking the tiles round-robin, the
+// vectors of a launch innermost (the copies of one tile for every vector run
+// back to back on neighbouring CTAs, so that the operator boxes they share are
+// read from DRAM once and then served from L2).  One output
 // tile (128 x 128) accumulates the K-segments of its block (the term sum of
 // the sigma reduction happens in the accumulator).  bf16 "pieces": an operand x is held as hi + lo; with
 // nsplit = 2 each product runs as hi*hi + hi*lo + lo*hi.
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
             ++q;
         };
         for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
-            const int tix = t % ntiles, v = t / ntiles;
+            const int tix = t / nvec, v = t % nvec;
             const Tile T = tiles[tix];
             const int nst = tile_stages(T, segs);
             if (nst == 0) {
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
             if (!ok) { failed = true; break; }
             __syncwarp();
             tc_fence_after();
-            const int tix = t % ntiles, v = t / ntiles;
+            const int tix = t / nvec, v = t % nvec;
             const Tile T = tiles[tix];
             const int nst = tile_stages(T, segs);
             epilogue_tile<NSPLIT>(T, v, nst, tmem + buf * TMEM_COLS, warp, lane, B, smem_u32(&tempty_bar[buf]));
@@ -466,8 +469,8 @@ __global__ void __launch_bounds__(THREADS3, 1)
         if (lane == 0) {
             uint32_t q = 0;
             for (int t = blockIdx.x; t < total && !failed; t += gridDim.x) {
-                const int v = t / ntiles;
-                const Tile T = tiles[t % ntiles];
+                const int v = t % nvec;
+                const Tile T = tiles[t / nvec];
                 const int nst = T.nst;
                 // a second 64-row (or 64-column) half only when the block extends past the first
                 const int ncol = min(T.tn, T.n - T.n0);  // columns of this tile
@@ -569,11 +572,11 @@ __global__ void __launch_bounds__(THREADS3, 1)
         // ---------------- epilogue ----------------
         uint32_t tc = 0;
         Tile Tn{};
-        if (blockIdx.x < total) Tn = tiles[blockIdx.x % ntiles];
+        if (blockIdx.x < total) Tn = tiles[blockIdx.x / nvec];
         for (int t = blockIdx.x; t < total && !failed; t += gridDim.x, ++tc) {
             const uint32_t buf = tc & 1u, use = tc >> 1;
             const Tile T = Tn;  // fetched one tile ahead, while the MMAs of this one run
-            if (t + (int)gridDim.x < total) Tn = tiles[(t + gridDim.x) % ntiles];
+            if (t + (int)gridDim.x < total) Tn = tiles[(t + gridDim.x) / nvec];
             int ok = 1;
             if (lane == 0) ok = mbar_wait(smem_u32(&tfull_bar[buf]), use & 1u) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);  // warp-uniform (tcgen05.ld is warp-collective)
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(THREADS3, 1)
             }
             __syncwarp();
             tc_fence_after();
-            epilogue_tile<NSPLIT>(T, t / ntiles, T.nst, tmem + buf * TMEM_COLS, warp, lane, B,
+            epilogue_tile<NSPLIT>(T, t % nvec, T.nst, tmem + buf * TMEM_COLS, warp, lane, B,
                                   smem_u32(&tempty_bar[buf]));
         }
     }

@@ -11,6 +11,7 @@
 #include <fstream>
 #include <unordered_map>
 
+#include "bond.h"
 #include "plan.h"
 
 namespace dmrg {
@@ -144,6 +145,7 @@ double* Plan::alloc(int64_t n) {
     }
     dev_bytes += bytes;
     stats.device_bytes = dev_bytes;
+    stats.device_bytes_peak = std::max(stats.device_bytes_peak, dev_bytes);
     return (double*)p;
 }
 
@@ -169,6 +171,7 @@ __nv_bfloat16* Plan::alloc_bf16(int64_t n) {
     }
     dev_bytes += bytes;
     stats.device_bytes = dev_bytes;
+    stats.device_bytes_peak = std::max(stats.device_bytes_peak, dev_bytes);
     return (__nv_bfloat16*)p;
 }
 
@@ -242,18 +245,18 @@ Plan::~Plan() {
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (d_sig_io) free(d_sig_io, n_sig_io);
-    for (auto& b : left)
-        if (b) {
-            if (b->d) free(b->d, b->n);
-            free_bf16(b->h, b->n);
-            free_lo(b->l, b->n);
-        }
-    for (auto& b : right)
-        if (b) {
-            if (b->d) free(b->d, b->n);
-            free_bf16(b->h, b->n);
-            free_lo(b->l, b->n);
-        }
+    for (auto* side : {&left, &right})
+        for (auto& b : *side)
+            if (b) {
+                try {
+                    tier_release(*this, *b);
+                } catch (...) {
+                }
+                if (b->d) free(b->d, b->n);
+                free_bf16(b->h, b->n);
+                free_lo(b->l, b->n);
+            }
+    tier_destroy(*this);
     free_bf16(s_hi, n_spc);
     free_lo(s_lo, n_spc);
     free_bf16(ps_hi, n_ppc);

@@ -132,6 +132,18 @@ struct Block {
     __nv_bfloat16* h = nullptr;  // bf16 pieces (mixed precision)
     __nv_bfloat16* l = nullptr;
     int64_t n = 0;
+    // host tier (a block is immutable once built, so one host copy serves every
+    // later eviction): which arrays exist, the pinned copy, and the copy events
+    bool has_d = false, has_h = false, has_l = false;
+    bool dev = true;               // device arrays allocated
+    bool host_valid = false;       // pinned copy written (complete once ev_out has)
+    bool evicting = false;         // device arrays freed once ev_out completes
+    bool fetching = false;         // device arrays valid once ev_in completes
+    char* host = nullptr;
+    int64_t host_cap = 0;
+    cudaEvent_t ev_out = nullptr;  // copy to host done
+    cudaEvent_t ev_use = nullptr;  // the compute stream's last use before an eviction
+    cudaEvent_t ev_in = nullptr;   // copy back to the device done
 };
 
 struct Plan {
@@ -249,6 +261,12 @@ struct Plan {
         int64_t per_solve = 1 << 14;
         int64_t pairs = 0;
     } harvest;
+
+    // host tier of the environment blocks (host_tier option): copy stream,
+    // pinned buffers released by freed blocks (reused best fit)
+    cudaStream_t copy_stream = nullptr;
+    std::vector<std::pair<char*, int64_t>> host_pool;
+    int64_t host_bytes = 0;
 
     double* alloc(int64_t n);
     void free(double*& p, int64_t n);

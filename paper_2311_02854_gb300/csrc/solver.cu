@@ -1036,6 +1036,7 @@ dmrg_status sweep(Plan& P, int n_sweeps, const int* D_schedule, double* energies
         for (auto& step : steps) {
             const int k = step.first;
             if (P.bond != k) set_bond(P, k);
+            tier_policy(P, k, step.second);  // copies overlap this bond's Davidson
             int iters = 0;
             dmrg_status s = davidson(P, psi, nr, P.opt.tol, P.opt.max_iter, P.opt.precond, en.data(), &iters);
             if (s == DMRG_ENOTCONV) last = s;
