@@ -141,8 +141,9 @@ typedef struct {
                                copy stream, while the bond's Davidson runs (blocks never change
                                after they are built); the next bond's block is copied back on
                                the same stream, and the compute stream waits for it where it is
-                               first used.  Results are bitwise those of host_tier = 0.  A failed
-                               pinned allocation returns DMRG_ENOMEM; default 0 */
+                               first used.  The arithmetic is that of host_tier = 0 on the same
+                               data (FP64 sweeps agree bitwise).  A failed pinned allocation
+                               returns DMRG_ENOMEM; default 0 */
 } dmrg_options;
 
 typedef struct {

@@ -3,8 +3,8 @@
 //
 // Each matrix is padded to a multiple of BB and cut into BB x BB blocks.  A
 // sweep pairs the blocks round-robin; in every round each pair (I, J) has its
-// 2BB x 2BB diagonal subproblem diagonalised approximately (one cyclic Jacobi
-// sweep in shared memory, giving an orthogonal Q), after which A <- Q^T A Q
+// 2BB x 2BB diagonal subproblem diagonalised (a few cyclic Jacobi sweeps in
+// shared memory, giving an orthogonal Q), after which A <- Q^T A Q
 // and V <- V Q are applied to the block rows and columns I, J as 2BB-wide
 // products by many CTAs.  Traffic per sweep is O(n^3 / BB) instead of the
 // O(n^3) of the element-wise Jacobi, and a round keeps nb/2 x n/(2BB) CTAs
@@ -35,6 +35,10 @@ constexpr double kStall64 = 0.5, kStallFrom64 = 1e-10;
 // two-stage FP64 sweeps: couplings between two states below kTau |A|_F are
 // left alone (they only mix weights no truncation can keep)
 constexpr double kTau = 1e-12;
+// cyclic sweeps at most per 2BB x 2BB subproblem (FP32 stage, FP64 sweeps):
+// solving the subproblems further cuts the outer sweeps, whose rotations of
+// block rows and columns cost O(n^3 / BB) memory traffic each
+constexpr int kInner32 = 3, kInner64 = 4;
 
 template <typename T>
 struct BJMat {
@@ -110,15 +114,17 @@ __device__ __forceinline__ int sub_index(const PairRef<T>& p, int a) {
     return a < BB ? p.I * BB + a : p.J * BB + a - BB;
 }
 
-// Q of each job (SB x SB, row-major) from one cyclic Jacobi sweep over its subproblem
+// Q of each job (SB x SB, row-major) from cyclic Jacobi sweeps over its
+// subproblem: up to max_inner sweeps, fewer once a sweep rotates nothing
 template <typename T>
 __global__ void __launch_bounds__(NT) bj_solve(const BJMat<T>* __restrict__ mats, const int* __restrict__ job_off,
-                                              int nmat, int round, T* __restrict__ Qall) {
+                                              int nmat, int round, T* __restrict__ Qall, int max_inner) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* S = reinterpret_cast<T*>(sm_raw);  // SB x LD
     T* Qs = S + SB * LD;                   // SB x LD
     __shared__ T cs[BB], sn[BB];
     __shared__ int pp[BB], qq[BB];
+    __shared__ int rotated;
     const PairRef<T> pr = pair_of(mats, job_off, nmat, round, blockIdx.x);
     T* Q = Qall + (int64_t)blockIdx.x * SB * SB;
     const int tid = threadIdx.x;
@@ -128,7 +134,9 @@ __global__ void __launch_bounds__(NT) bj_solve(const BJMat<T>* __restrict__ mats
         Qs[a * LD + b] = (a == b) ? T(1) : T(0);
     }
     __syncthreads();
-    if (pr.live) {
+    for (int sw = 0; pr.live && sw < max_inner; ++sw) {
+        if (tid == 0) rotated = 0;
+        __syncthreads();
         for (int r = 0; r < SB - 1; ++r) {
             if (tid < BB) {
                 int p, q;
@@ -142,6 +150,7 @@ __global__ void __launch_bounds__(NT) bj_solve(const BJMat<T>* __restrict__ mats
                     const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
                     c = T(1) / sqrt(T(1) + t * t);
                     s = t * c;
+                    if (s != T(0)) rotated = 1;
                 }
                 cs[tid] = c;
                 sn[tid] = s;
@@ -175,6 +184,9 @@ __global__ void __launch_bounds__(NT) bj_solve(const BJMat<T>* __restrict__ mats
             }
             __syncthreads();
         }
+        const int any = rotated;  // read by every thread before the next reset
+        __syncthreads();
+        if (!any) break;
     }
     for (int e = tid; e < SB * SB; e += NT) Q[e] = Qs[(e / SB) * LD + e % SB];
 }
@@ -421,7 +433,7 @@ __global__ void __launch_bounds__(NT) bj_store(const BJMat<double>* __restrict__
 template <typename T>
 int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
               int ne_max, int ntile, T* Qall, double* d_norm, int max_sweeps, double tol, double stall,
-              double stall_from, cudaStream_t st, std::vector<double>* hist, double* final_worst) {
+              double stall_from, int max_inner, cudaStream_t st, std::vector<double>* hist, double* final_worst) {
     const size_t smem = 2 * SB * LD * sizeof(T);
     static bool attr = false;
     if (!attr) {
@@ -449,7 +461,7 @@ int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
         if (prev >= 0.0 && worst < stall_from * stall_from && worst > stall * stall * prev) break;
         prev = worst;
         for (int r = 0; r < ne_max - 1; ++r) {
-            bj_solve<T><<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall);
+            bj_solve<T><<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, max_inner);
             bj_rows<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
             bj_cols<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
             launch_counter() += 3;
@@ -558,7 +570,7 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
         DMRG_CHECK_CUDA(cudaMemcpyAsync(d_m32, m32.data(), sizeof(BJMat<float>) * nmat, cudaMemcpyHostToDevice, st));
         // stage 1: FP32 sweeps down to the FP32 rounding level
         const int s32 = bj_sweeps<float>(d_m32, d_off, nmat, njob, ne_max, ntile, (float*)Qall, d_norm,
-                                         kMaxSweeps32, kTol32, kStall32, kStallFrom32, st, hist, &worst);
+                                         kMaxSweeps32, kTol32, kStall32, kStallFrom32, kInner32, st, hist, &worst);
         if (sweeps32_out) *sweeps32_out = s32;
         // stage 2 (FP64): V = V32 made orthonormal by two Newton-Schulz steps
         // V <- V (3 I - V^T V) / 2, then A = V^T rho V
@@ -591,7 +603,7 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
     }
     // FP64 sweeps to the tolerance
     const int sweeps = bj_sweeps<double>(d_mats, d_off, nmat, njob, ne_max, ntile, Qall, d_norm, max_sweeps, tol,
-                                         kStall64, kStallFrom64, st, hist, &worst);
+                                         kStall64, kStallFrom64, kInner64, st, hist, &worst);
     bj_store<<<dim3(gx, nmat), NT, 0, st>>>(d_mats, d_jobs);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());
