@@ -216,9 +216,14 @@ void dmrg_default_options(dmrg_options* opt);
 
 /* Create a plan (Sec. 2.3: qops of a bond, Eq. Hsq integrals).
  *  h        K*K row-major one-electron integrals (host), copied.
- *  chol     n_chol*K*K Cholesky vectors L[X][p][q] (host), copied; the
- *           two-electron integrals are (pq|rs) = sum_X L[X][p][q] L[X][r][s],
+ *  chol     n_chol > 0: n_chol*K*K Cholesky vectors L[X][p][q] (host), copied;
+ *           the two-electron integrals are (pq|rs) = sum_X L[X][p][q] L[X][r][s],
  *           formed on the device.
+ *           n_chol = 0: the full K*K*K*K array of chemist-notation integrals
+ *           (pq|rs) at [((p*K + q)*K + r)*K + s] (host), copied; K <= 128; it
+ *           must have the symmetry of real orbitals, (pq|rs) = (qp|rs) =
+ *           (pq|sr) = (rs|pq) to 1e-12 of its largest entry (DMRG_EINVAL
+ *           otherwise).
  *  e_core   constant energy added to reported energies.
  *  K,N,twoS orbitals, electrons, 2*Sz; N <= 2K, |twoS| <= min(N, 2K-N),
  *           N + twoS even.
@@ -226,7 +231,8 @@ void dmrg_default_options(dmrg_options* opt);
  *  mps_path binary MPS file (format of synthetic_inputs.write_mps): sectors
  *           of every bond and block-sparse site tensors, left-orthonormal
  *           left of the centre, right-orthonormal right of centre+1.
- * Returns DMRG_EINVAL on inconsistent sizes or file, DMRG_EIO if unreadable. */
+ * Returns DMRG_EINVAL on inconsistent sizes or file, DMRG_ENUMERIC on a
+ * non-finite integral, DMRG_EIO if the file is unreadable. */
 dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_core,
                       int K, int N, int twoS, int D, const dmrg_options* opt,
                       const char* mps_path, dmrg_plan_t* out);
@@ -462,6 +468,17 @@ dmrg_status dmrg_grouped_gemm_noalloc(int n_out, const int* m, const int* n, con
 
 /* Size in bytes of the static work-list array of dmrg_grouped_gemm_noalloc. */
 int64_t dmrg_noalloc_scratch_bytes(void);
+
+/* Check of the bounded device waits every warp-specialised kernel of the
+ * library uses (mbarrier waits that give up after a time limit and set a device
+ * error word instead of spinning forever).  One CTA initialises an mbarrier,
+ * arrives on it only if `arrive` is nonzero, and waits on it for at most
+ * `seconds` (0 < seconds <= 2) with the kernels' wait routine; no copy or MMA is
+ * in flight.  Returns DMRG_OK if the wait completed, DMRG_ETIMEOUT if it gave up
+ * (the status the library's kernels report through their error words), and
+ * leaves the context usable either way.  DMRG_EINVAL for seconds outside the
+ * range.  Synchronises the stream. */
+dmrg_status dmrg_selftest_wait(double seconds, int arrive, void* stream);
 
 /* Library build / device information: writes a short string. */
 const char* dmrg_version(void);

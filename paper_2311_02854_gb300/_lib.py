@@ -104,6 +104,7 @@ _SIGS = {
     "dmrg_mlp_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_int]),
     "dmrg_mlp_num_params": (C.c_int, []),
     "dmrg_extrapolate": (C.c_int, [_D, _D, C.c_int, _D, _D, _D]),
+    "dmrg_selftest_wait": (C.c_int, [C.c_double, C.c_int, _P]),
 }
 
 
@@ -169,7 +170,9 @@ def default_options(**kw):
 
 
 class Plan:
-    """dmrg_plan: integrals + MPS file -> plan.  ``close()`` calls dmrg_destroy."""
+    """dmrg_plan: integrals + MPS file -> plan.  ``chol`` is either the
+    Cholesky vectors (n_chol x K x K) or the full (pq|rs) array (K x K x K x K).
+    ``close()`` calls dmrg_destroy."""
 
     def __init__(self, h, chol, K, N, twoS, D, mps_path, e_core=0.0, options=None, **kw):
         L = lib()
@@ -178,7 +181,9 @@ class Plan:
         opts = options if options is not None else default_options(**kw)
         self.options = opts
         handle = _P()
-        code = L.dmrg_plan(_dptr(self._h), _dptr(self._chol), int(self._chol.shape[0]), float(e_core),
+        # a 4-index array is the full (pq|rs) (n_chol = 0), else Cholesky vectors
+        n_chol = 0 if self._chol.ndim == 4 else int(self._chol.shape[0])
+        code = L.dmrg_plan(_dptr(self._h), _dptr(self._chol), n_chol, float(e_core),
                            int(K), int(N), int(twoS), int(D), C.byref(opts), str(mps_path).encode(),
                            C.byref(handle))
         _check(code, None)
@@ -398,6 +403,13 @@ def extrapolate(w, E):
     code = lib().dmrg_extrapolate(_dptr(w), _dptr(E), int(w.size), C.pointer(e0), C.pointer(a), C.pointer(r))
     _check(code, None)
     return e0.value, a.value, r.value
+
+
+def selftest_wait(seconds, arrive, stream=None):
+    """dmrg_selftest_wait: one bounded device wait on an mbarrier that is
+    arrived on (``arrive``) or not; raises DMRGError(DMRG_ETIMEOUT) when the
+    wait gave up."""
+    _check(lib().dmrg_selftest_wait(float(seconds), int(arrive), _stream(stream)), None)
 
 
 def noalloc_scratch_bytes():

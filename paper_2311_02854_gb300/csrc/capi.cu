@@ -169,15 +169,35 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
                       int D, const dmrg_options* opt, const char* mps_path, dmrg_plan_t* out) {
     if (!out) return fail(nullptr, DMRG_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!h || !chol || n_chol <= 0 || K < 2 || K > 512 || N < 0 || N > 2 * K || D < 1)
+    if (!h || !chol || n_chol < 0 || K < 2 || K > 512 || N < 0 || N > 2 * K || D < 1)
         return fail(nullptr, DMRG_EINVAL, "bad sizes");
+    if (n_chol == 0 && K > 128) return fail(nullptr, DMRG_EINVAL, "a full (pq|rs) array is accepted up to K = 128");
     if (((N + twoS) & 1) || std::abs(twoS) > std::min(N, 2 * K - N))
         return fail(nullptr, DMRG_EINVAL, "inconsistent N / 2Sz");
     if (!mps_path) return fail(nullptr, DMRG_EINVAL, "an MPS file is required");
     for (int64_t i = 0; i < (int64_t)K * K; ++i)
         if (!std::isfinite(h[i])) return fail(nullptr, DMRG_ENUMERIC, "non-finite one-electron integral");
-    for (int64_t i = 0; i < (int64_t)n_chol * K * K; ++i)
-        if (!std::isfinite(chol[i])) return fail(nullptr, DMRG_ENUMERIC, "non-finite Cholesky vector");
+    const int64_t n_in = n_chol > 0 ? (int64_t)n_chol * K * K : (int64_t)K * K * K * K;
+    for (int64_t i = 0; i < n_in; ++i)
+        if (!std::isfinite(chol[i]))
+            return fail(nullptr, DMRG_ENUMERIC, n_chol > 0 ? "non-finite Cholesky vector" : "non-finite (pq|rs)");
+    if (n_chol == 0) {
+        // real orbitals: (pq|rs) = (qp|rs) = (pq|sr) = (rs|pq)
+        const int64_t K2 = (int64_t)K * K;
+        double amax = 0.0, dmax = 0.0;
+        for (int64_t i = 0; i < K2 * K2; ++i) amax = std::max(amax, std::fabs(chol[i]));
+        for (int p = 0; p < K; ++p)
+            for (int q = 0; q < K; ++q)
+                for (int r = 0; r < K; ++r)
+                    for (int t = 0; t < K; ++t) {
+                        const double x = chol[((int64_t)p * K + q) * K2 + r * K + t];
+                        dmax = std::max(dmax, std::fabs(x - chol[((int64_t)q * K + p) * K2 + r * K + t]));
+                        dmax = std::max(dmax, std::fabs(x - chol[((int64_t)p * K + q) * K2 + t * K + r]));
+                        dmax = std::max(dmax, std::fabs(x - chol[((int64_t)r * K + t) * K2 + p * K + q]));
+                    }
+        if (dmax > 1e-12 * std::max(amax, 1.0))
+            return fail(nullptr, DMRG_EINVAL, "(pq|rs) lacks the symmetry of real orbitals");
+    }
     auto* plan = new dmrg_plan_s();
     dmrg_status st = guarded(plan, [&]() -> dmrg_status {
         Plan& P = plan->P;
@@ -213,8 +233,14 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         size_t freeb = 0, totb = 0;
         DMRG_CHECK_CUDA(cudaMemGetInfo(&freeb, &totb));
         P.budget = P.opt.mem_budget > 0 ? P.opt.mem_budget : (int64_t)(0.9 * (double)freeb);
-        // (pq|rs) = sum_X L[X][pq] L[X][rs] on the device
         const int64_t K2 = (int64_t)K * K;
+        P.left.resize(K + 1);
+        P.right.resize(K + 1);
+        if (n_chol == 0) {  // the full array as given
+            P.I.eri.assign(chol, chol + K2 * K2);
+            return DMRG_OK;
+        }
+        // (pq|rs) = sum_X L[X][pq] L[X][rs] on the device
         double* dL = P.alloc(n_chol * K2);
         double* dE = P.alloc(K2 * K2);
         DMRG_CHECK_CUDA(cudaMemcpy(dL, chol, n_chol * K2 * 8, cudaMemcpyHostToDevice));
@@ -241,8 +267,6 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
         wl.release();
         P.free(dL, n_chol * K2);
         P.free(dE, K2 * K2);
-        P.left.resize(K + 1);
-        P.right.resize(K + 1);
         return DMRG_OK;
     });
     if (st != DMRG_OK) {
@@ -697,5 +721,15 @@ dmrg_status dmrg_grouped_gemm_noalloc(int n_out, const int* m, const int* n, con
 }
 
 int64_t dmrg_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
+
+dmrg_status dmrg_selftest_wait(double seconds, int arrive, void* stream) {
+    if (!(seconds > 0.0 && seconds <= 2.0)) return fail(nullptr, DMRG_EINVAL, "seconds must lie in (0, 2]");
+    try {
+        if (wait_selftest(seconds, arrive != 0, (cudaStream_t)stream)) return DMRG_OK;
+        return fail(nullptr, DMRG_ETIMEOUT, "bounded device wait gave up (self-test)");
+    } catch (const Error& e) {
+        return fail(nullptr, e.code, e.what());
+    }
+}
 
 }  // extern "C"

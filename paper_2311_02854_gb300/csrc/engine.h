@@ -121,5 +121,7 @@ void dev_fill(double* x, double v, int64_t n, cudaStream_t st);
 void dev_perturb(double* x, int64_t n, uint32_t seed, double amp, cudaStream_t st);
 void dev_identity(double* x, int n, cudaStream_t st);
 int64_t& launch_counter();
+// selftest.cu: one bounded mbarrier wait (arrived on or not); false if it gave up
+bool wait_selftest(double seconds, bool arrive, cudaStream_t st);
 
 }  // namespace dmrg

@@ -33,11 +33,11 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 // Wait until the phase with the given parity has completed; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try(addr, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_try(addr, parity)) {
-        if (gtimer() - t0 > kWaitLimitNs) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
     return true;
 }

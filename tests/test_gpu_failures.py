@@ -66,3 +66,28 @@ def test_unreadable_mps_file_gives_eio(tmp_path):
     with pytest.raises(g.DMRGError) as e:
         g.Plan(h, L, 6, 6, 0, 20, str(bad))
     assert e.value.code in (-7, -1)
+
+
+def test_bounded_wait_gives_etimeout_and_the_context_stays_usable(tmp_path):
+    """A wait on an mbarrier that nothing arrives on (the wait routine of the
+    tensor-core kernels, with a 0.2 s limit) gives up and reports
+    DMRG_ETIMEOUT; the same wait with an arrival completes, and a sigma runs
+    afterwards."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    with pytest.raises(g.DMRGError) as e:
+        g.selftest_wait(0.2, arrive=False)
+    assert e.value.code == -5
+    g.selftest_wait(0.2, arrive=True)
+    with pytest.raises(g.DMRGError) as e:
+        g.selftest_wait(3.0, arrive=True)
+    assert e.value.code == -1
+    K, N, twoS, D, k = 6, 6, 0, 20, 3
+    h, L, mps, path = make_case(tmp_path, K, N, twoS, D, center=k)
+    plan = g.Plan(h, L, K, N, twoS, D, path, precision=1)
+    plan.set_bond(k)
+    x = torch.from_numpy(si.random_vector(plan.dim, seed=1)).cuda()
+    y = torch.empty_like(x)
+    plan.sigma(x, y)
+    assert np.isfinite(y.cpu().numpy()).all()
+    plan.close()

@@ -265,3 +265,31 @@ def make_dim(g, h, L, K, N, twoS, D, path, k):
     d = plan.dim
     plan.close()
     return d
+
+
+def test_plan_from_full_eri_array(tmp_path):
+    """n_chol = 0: the plan takes the full (pq|rs) array; sigma equals the
+    Cholesky-built plan's to rounding, and an array without the real-orbital
+    symmetry is refused."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    K, N, k = 8, 8, 4
+    h, L, mps, path = make_case(tmp_path, K, N, 0, 64, center=k)
+    eri = eri_from_cholesky(L)
+    ys = []
+    for ints in (L, eri):
+        plan = g.Plan(h, ints, K, N, 0, 64, path)
+        plan.set_bond(k)
+        x = torch.from_numpy(si.random_vector(plan.dim, seed=1)).cuda()
+        y = torch.empty_like(x)
+        plan.sigma(x, y)
+        ys.append(y.cpu().numpy())
+        plan.close()
+    err = np.linalg.norm(ys[1] - ys[0]) / np.linalg.norm(ys[0])
+    print(f"full (pq|rs) vs Cholesky plan: sigma rel diff {err:.2e}")
+    assert err < 1e-13
+    bad = eri.copy()
+    bad[0, 1, 2, 3] += 1e-3
+    with pytest.raises(g.DMRGError) as exc:
+        g.Plan(h, bad, K, N, 0, 64, path)
+    assert exc.value.code == -1
