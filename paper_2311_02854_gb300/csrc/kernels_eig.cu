@@ -3,8 +3,8 @@
 //
 // Each matrix is padded to a multiple of BB and cut into BB x BB blocks.  A
 // sweep pairs the blocks round-robin; in every round each pair (I, J) has its
-// 2BB x 2BB diagonal subproblem diagonalised (a few cyclic Jacobi sweeps in
-// shared memory, giving an orthogonal Q), after which A <- Q^T A Q
+// 2BB x 2BB diagonal subproblem diagonalised approximately (cyclic Jacobi
+// sweeps in shared memory, giving an orthogonal Q), after which A <- Q^T A Q
 // and V <- V Q are applied to the block rows and columns I, J as 2BB-wide
 // products by many CTAs.  Traffic per sweep is O(n^3 / BB) instead of the
 // O(n^3) of the element-wise Jacobi, and a round keeps nb/2 x n/(2BB) CTAs
@@ -35,10 +35,10 @@ constexpr double kStall64 = 0.5, kStallFrom64 = 1e-10;
 // two-stage FP64 sweeps: couplings between two states below kTau |A|_F are
 // left alone (they only mix weights no truncation can keep)
 constexpr double kTau = 1e-12;
-// cyclic sweeps at most per 2BB x 2BB subproblem (FP32 stage, FP64 sweeps):
-// solving the subproblems further cuts the outer sweeps, whose rotations of
-// block rows and columns cost O(n^3 / BB) memory traffic each
-constexpr int kInner32 = 3, kInner64 = 4;
+// cyclic sweeps at most per 2BB x 2BB subproblem (FP32 stage, FP64 sweeps).
+// One: solving the subproblems further (3 / 4 sweeps) made the K = 73
+// decimations slower (more outer FP64 sweeps, 2.1 -> 3.2 s per call)
+constexpr int kInner32 = 1, kInner64 = 1;
 
 template <typename T>
 struct BJMat {
