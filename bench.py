@@ -458,7 +458,9 @@ def run_sigma_probe(args):
     nv = max(1, args.nvec)
     # nvec > 1: the plan launches nvec vectors per grouped launch (several
     # Davidson vectors / roots at once); compared with nvec single-vector calls
-    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision], n_roots=nv)
+    extra_opts = {"sigma_per_term": 1, "sigma_tile_n": 128} if args.per_term else {}
+    plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision], n_roots=nv,
+                  **extra_opts)
     plan.set_bond(k)
     x = torch.from_numpy(np.concatenate([si.random_vector(plan.dim, seed=1 + v) for v in range(nv)])).cuda()
     y = torch.empty_like(x)
@@ -486,6 +488,8 @@ def run_sigma_probe(args):
         t1 = timed(lambda: [plan.sigma(x[v * d:(v + 1) * d], y[v * d:(v + 1) * d]) for v in range(nv)])
         extra = {"nvec": nv, "sigma_ms_one_vector_per_call": round(t1, 3),
                  "sigma_tflops_one_vector_per_call": round(nv * st["sigma_flops"] / t1 / 1e9, 3)}
+    extra["launch_pairs_per_sigma"] = st["sigma_chunks"]
+    extra["per_term"] = bool(args.per_term)
     print(json.dumps({"mode": "sigma-only", "workload": args.workload, "precision": args.precision,
                       "sigma_ms": round(t, 3), "sigma_tflops": round(nv * st["sigma_flops"] / t / 1e9, 3), **extra,
                       "sigma_flops": st["sigma_flops"], "tiles": st["sigma_tiles"], "stages": st["sigma_stages"],
@@ -650,6 +654,8 @@ def main():
                     help="mixed modes with --fp64-store 1: FP64 products on the FP64-accurate tensor-core engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvec", type=int, default=1, help="--sigma-only: vectors per grouped sigma launch")
+    ap.add_argument("--per-term", action="store_true",
+                    help="--sigma-only: one phase-1 / phase-2 launch pair per Hamiltonian term (baseline)")
     ap.add_argument("--sigma-only", action="store_true",
                     help="time sigma calls at the middle bond (NVTX range 'sigma'); for profiling")
     ap.add_argument("--mlp-study", action="store_true",

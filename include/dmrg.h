@@ -144,6 +144,11 @@ typedef struct {
                                first used.  The arithmetic is that of host_tier = 0 on the same
                                data (FP64 sweeps agree bitwise).  A failed pinned allocation
                                returns DMRG_ENOMEM; default 0 */
+    int sigma_per_term;     /* mixed modes, for measurement: 1 = the sigma work list is cut into
+                               one scratch chunk per Hamiltonian term, i.e. a phase-1 and a
+                               phase-2 launch per term (a launch-per-term baseline of the
+                               grouped launch; Sec. 2.3 batches GEMMs per term); no tuning;
+                               default 0 */
 } dmrg_options;
 
 typedef struct {

@@ -27,7 +27,8 @@ class Options(C.Structure):
                 ("mem_budget", C.c_int64), ("scratch_bytes", C.c_int64), ("keep_envs", C.c_int),
                 ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int),
                 ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int), ("refine", C.c_int), ("max_refine", C.c_int),
-                ("fp64_tc", C.c_int), ("host_tier", C.c_int)]
+                ("fp64_tc", C.c_int), ("host_tier", C.c_int),
+                ("sigma_per_term", C.c_int)]
 
 
 class Stats(C.Structure):

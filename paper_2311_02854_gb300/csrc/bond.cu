@@ -872,6 +872,7 @@ void set_bond(Plan& P, int k) {
                     c.n = o.dr;
                     c.alpha = t.c * zeta * mv;
                     c.qsec = (int)si;
+                    c.term = (int)ti;
                     out.push_back(c);
                 }
             }
@@ -911,8 +912,10 @@ void set_bond(Plan& P, int k) {
         SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
         const double t_terms = host_ms_since(hs0);
         if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
-        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0) shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
+        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0 && !P.opt.sigma_per_term)
+            shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
         const double t_tune = host_ms_since(hs0);
+        tl.chunk_per_term = P.opt.sigma_per_term != 0;
         tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, cap, shape.kchunk, TC_ATOMIC_F64, vs, G, shape.tn);
         const double t_lower = host_ms_since(hs0);
         P.stats.sigma_tile_n = shape.tn;

@@ -159,6 +159,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->max_refine = 0;
     o->fp64_tc = 0;
     o->host_tier = 0;
+    o->sigma_per_term = 0;
 }
 
 const char* dmrg_version(void) {

@@ -632,6 +632,7 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         size_t j = i;
         for (; j < cs.size(); ++j) {
             const Contrib& c = cs[j];
+            if (chunk_per_term && j > i && c.term != cs[i].term) break;
             const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
             const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
             Item it;

@@ -78,6 +78,7 @@ struct Contrib {
     int m, k1, k2, n;
     double alpha;
     int qsec = -1;  // sigma: wavefunction sector read by Q (for the padded bf16 copy)
+    int term = -1;  // sigma: index of the Hamiltonian term the product belongs to
 };
 struct OutBlock {
     int8_t buf;
@@ -96,6 +97,7 @@ struct ProductList {
     int8_t sbuf = -1;  // buffer id of the phase-1 scratch
     bool tc = false;
     int tile_m = 0, tile_n = 0;  // FP64-engine tile shape of lower() (0: the engine's default)
+    bool chunk_per_term = false;  // lower_tma: a new scratch chunk (launch pair) at every term
     void clear();
     // FP64 engine: per-segment alpha, 64x64 tiles
     void lower(int8_t scratch_buf, int8_t ident_buf, int ident_ld, int64_t scratch_cap, int64_t kchunk);

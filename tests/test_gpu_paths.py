@@ -63,6 +63,32 @@ def test_sigma_in_several_scratch_chunks(tmp_path, prec):
     assert rel_err(got, out[0][1]) <= (1e-14 if prec == FP64 else 1e-5)
 
 
+def test_sigma_one_launch_pair_per_term(tmp_path):
+    """sigma_per_term = 1 (the launch-per-term baseline): one scratch chunk per
+    Hamiltonian term, so as many launch pairs as terms with products; the
+    result equals the oracle's like the grouped launch's."""
+    torch = cuda_torch()
+    g = gpu_lib()
+    K, N, twoS, D, k = 8, 8, 0, 64, 4
+    h, L, mps, path = make_case(tmp_path, K, N, twoS, D, center=k)
+    ts, psi, ref = _oracle_sigma(h, L, N, twoS, mps, k)
+    res = {}
+    for pt in (0, 1):
+        plan = g.Plan(h, L, K, N, twoS, D, path, precision=1, sigma_per_term=pt, sigma_tile_n=128)
+        plan.set_bond(k)
+        st = plan.stats()
+        x = torch.from_numpy(psi[0].copy()).cuda()
+        y = torch.empty_like(x)
+        plan.sigma(x, y)
+        torch.cuda.synchronize()
+        res[pt] = (st["sigma_chunks"], st["n_terms"], y.cpu().numpy())
+        plan.close()
+    print(f"launch pairs: grouped {res[0][0]}, per term {res[1][0]} ({res[1][1]} terms); "
+          f"rel err {rel_err(res[1][2], ref[0]):.2e}")
+    assert res[0][0] == 1 and res[1][0] > 10 * res[0][0] and res[1][0] <= res[1][1]
+    assert rel_err(res[1][2], ref[0]) <= TOL_MIXED
+
+
 def test_tensor_core_sigma_three_vectors_per_launch(tmp_path):
     """n_roots = 3: the mixed sigma launches three vectors per grouped launch;
     each is compared element by element with the oracle and with one-vector
