@@ -417,7 +417,7 @@ def accuracy_leg(g, torch, w, h, L, path, k, args):
     nrm2 = float(x @ x)
     rq_m = float(x @ wv) / nrm2
     res_m = float(torch.linalg.vector_norm(wv - rq_m * x)) / nrm2 ** 0.5
-    plan.set_refine(1, 8)
+    plan.set_refine(1, 12)
     t3 = time.perf_counter()
     er, itr, convr = plan.davidson(x, 1, tol=args.tol, max_iter=args.dav_iters)
     torch.cuda.synchronize()
