@@ -188,7 +188,7 @@ def run_mine(args):
     td = tempfile.mkdtemp(prefix="dmrg_bench_")
     h, L, bonds, path = make_inputs(w, td, k)
     plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=prec, tol=args.tol, max_iter=args.dav_iters,
-                  keep_envs=0, fp64_store=int(args.fp64_store), refine=int(args.refine),
+                  keep_envs=0, fp64_store=int(args.fp64_store), refine=int(args.refine), verbose=int(args.verbose),
                   fp64_tc=int(args.fp64_tc), scratch_bytes=int(args.scratch_gb * 2**30),
                   mem_budget=int(args.mem_budget_gb * 2**30))
     stream = torch.cuda.Stream()
@@ -467,7 +467,7 @@ def run_sigma_probe(args):
     # Davidson vectors / roots at once); compared with nvec single-vector calls
     extra_opts = {"sigma_per_term": 1, "sigma_tile_n": 128} if args.per_term else {}
     plan = g.Plan(h, L, K, w["N"], w["twoS"], D, path, precision=PRECISIONS[args.precision], n_roots=nv,
-                  **extra_opts)
+                  verbose=int(args.verbose), **extra_opts)
     plan.set_bond(k)
     x = torch.from_numpy(np.concatenate([si.random_vector(plan.dim, seed=1 + v) for v in range(nv)])).cuda()
     y = torch.empty_like(x)
@@ -661,6 +661,7 @@ def main():
                     help="mixed modes with --fp64-store 1: FP64 products on the FP64-accurate tensor-core engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nvec", type=int, default=1, help="--sigma-only: vectors per grouped sigma launch")
+    ap.add_argument("--verbose", type=int, default=0, help="library progress lines on stderr (planning times)")
     ap.add_argument("--per-term", action="store_true",
                     help="--sigma-only: one phase-1 / phase-2 launch pair per Hamiltonian term (baseline)")
     ap.add_argument("--sigma-only", action="store_true",

@@ -114,7 +114,9 @@ typedef struct {
                                8th output block, 16th beyond a million products, with all their
                                products); choices are cached by
                                the bond's sector-size histogram; ignored when tc_kchunk > 0
-                               or sigma_tile_n > 0; default 1 */
+                               or sigma_tile_n > 0, and for lists of over 2^20 products (which
+                               keep tile width 128 and the full K-chunk, the measured winner
+                               there); default 1 */
     int sigma_tile_n;       /* mixed modes: 64 or 128 fixes the tile width of the sigma work
                                lists (no tuning); 0 = tuned or 128; default 0 */
     int refine;             /* mixed modes: 1 = FP64 residual correction of Davidson (a defect
@@ -149,6 +151,9 @@ typedef struct {
                                phase-2 launch per term (a launch-per-term baseline of the
                                grouped launch; Sec. 2.3 batches GEMMs per term); no tuning;
                                default 0 */
+    double decim_tol32;     /* decimation eigensolver: off(rho)/|rho| at which the FP32 stage of
+                               large density-matrix blocks hands over to the FP64 sweeps (it also
+                               stops at the FP32 rounding floor); 0 => 1e-5 */
 } dmrg_options;
 
 typedef struct {

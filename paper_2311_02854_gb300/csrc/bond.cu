@@ -912,7 +912,11 @@ void set_bond(Plan& P, int k) {
         SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
         const double t_terms = host_ms_since(hs0);
         if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
-        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0 && !P.opt.sigma_per_term)
+        // lists of over a million products keep the default shape: it won every
+        // measurement at that size (K = 54 and K = 73 middle bonds), and the
+        // timing of the candidates costs 0.3-1 s per new bond there
+        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0 && !P.opt.sigma_per_term &&
+                 tl.cs.size() <= ((size_t)1 << 20))
             shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
         const double t_tune = host_ms_since(hs0);
         tl.chunk_per_term = P.opt.sigma_per_term != 0;
@@ -926,27 +930,42 @@ void set_bond(Plan& P, int k) {
             P.stats.sigma_load_bytes[ph][0] = P.stats.sigma_load_bytes[ph][1] = 0.0;
         }
         P.stats.sigma_mma_flops = 0.0;
-        for (const auto& ch : tl.tchunks)
-            for (int ph = 0; ph < 2; ++ph) {
-                const TmaWorkList& w = ph ? ch.second : ch.first;
-                P.stats.sigma_tiles[ph] += (int64_t)w.tiles.size();
-                for (const Tile& t : w.tiles) {
-                    int64_t kk = 0;
-                    for (int q = t.seg_beg; q < t.seg_end; ++q) kk += round_up(w.segs[q].k, 16);
-                    for (int q = t.seg_beg; q < t.seg_end; ++q) P.stats.sigma_stages[ph] += (w.segs[q].k + 63) / 64;
-                    P.stats.sigma_mma_flops += 2.0 * 128 * 128 * (double)kk;
-                    // operand bytes the TMA loads for this tile (boxes of 128-byte
-                    // rows, one per piece), split into scratch and everything else
-                    const int nA = (t.m - t.m0 > 64) ? 2 : 1, nB = (std::min(t.tn, t.n - t.n0) > 64) ? 2 : 1;
-                    for (int q = t.seg_beg; q < t.seg_end; ++q) {
-                        const TSeg& g = w.segs[q];
-                        const double st = (double)((g.k + 63) / 64) * P.nsplit * 128.0;
-                        const double ba = st * nA * g.a_br, bb = st * nB * g.b_br;
-                        P.stats.sigma_load_bytes[ph][tl.maps.keys[g.a_map].buf == BUF_SCR ? 1 : 0] += ba;
-                        P.stats.sigma_load_bytes[ph][tl.maps.keys[g.b_map].buf == BUF_SCR ? 1 : 0] += bb;
-                    }
+        // per (chunk, phase) on host threads, summed in order afterwards
+        struct TileCount {
+            int64_t tiles = 0, stages = 0;
+            double mma = 0.0, load[2] = {0.0, 0.0};
+        };
+        std::vector<TileCount> cnt(2 * tl.tchunks.size());
+        parallel_for(cnt.size(), [&](size_t x) {
+            const int ph = (int)(x & 1);
+            const TmaWorkList& w = ph ? tl.tchunks[x / 2].second : tl.tchunks[x / 2].first;
+            TileCount& c = cnt[x];
+            c.tiles = (int64_t)w.tiles.size();
+            for (const Tile& t : w.tiles) {
+                int64_t kk = 0;
+                for (int q = t.seg_beg; q < t.seg_end; ++q) kk += round_up(w.segs[q].k, 16);
+                for (int q = t.seg_beg; q < t.seg_end; ++q) c.stages += (w.segs[q].k + 63) / 64;
+                c.mma += 2.0 * 128 * 128 * (double)kk;
+                // operand bytes the TMA loads for this tile (boxes of 128-byte
+                // rows, one per piece), split into scratch and everything else
+                const int nA = (t.m - t.m0 > 64) ? 2 : 1, nB = (std::min(t.tn, t.n - t.n0) > 64) ? 2 : 1;
+                for (int q = t.seg_beg; q < t.seg_end; ++q) {
+                    const TSeg& g = w.segs[q];
+                    const double st = (double)((g.k + 63) / 64) * P.nsplit * 128.0;
+                    c.load[tl.maps.keys[g.a_map].buf == BUF_SCR ? 1 : 0] += st * nA * g.a_br;
+                    c.load[tl.maps.keys[g.b_map].buf == BUF_SCR ? 1 : 0] += st * nB * g.b_br;
                 }
             }
+        });
+        for (size_t x = 0; x < cnt.size(); ++x) {
+            const int ph = (int)(x & 1);
+            P.stats.sigma_tiles[ph] += cnt[x].tiles;
+            P.stats.sigma_stages[ph] += cnt[x].stages;
+            P.stats.sigma_mma_flops += cnt[x].mma;
+            P.stats.sigma_load_bytes[ph][0] += cnt[x].load[0];
+            P.stats.sigma_load_bytes[ph][1] += cnt[x].load[1];
+        }
+        const double t_count = host_ms_since(hs0);
         ensure_scratch(P, (int64_t)G * tl.scratch_elems);
         ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
         for (auto& ch : tl.tchunks) {
@@ -956,8 +975,9 @@ void set_bond(Plan& P, int k) {
         tl.maps.encode_upload(sigma_bufs(P, k, nullptr), P.nsplit, P.stream);
         if (P.opt.verbose)
             fprintf(stderr, "[dmrg] bond %d sigma planning: terms %.0f ms, tuning %.0f ms, lowering %.0f ms, "
-                            "upload %.0f ms (%zu chunks)\n",
-                    k, t_terms, t_tune - t_terms, t_lower - t_tune, host_ms_since(hs0) - t_lower, tl.tchunks.size());
+                            "counts %.0f ms, upload %.0f ms (%zu chunks)\n",
+                    k, t_terms, t_tune - t_terms, t_lower - t_tune, t_count - t_lower, host_ms_since(hs0) - t_count,
+                    tl.tchunks.size());
         P.stats.sigma_maps = (int64_t)tl.maps.keys.size();
         P.stats.sigma_flops = tl.flops;
         // padded bf16 copy of psi: one split job per sector

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(NT) bj_sym(const BJMat<double>* __restrict__ m
 int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double tol, cudaStream_t st,
                       const std::function<double*(int64_t)>& alloc_f,
                       const std::function<void(double*, int64_t)>& free_f, std::vector<double>* hist,
-                      int* sweeps32_out) {
+                      int* sweeps32_out, double tol32) {
     const int nmat = (int)jobs.size();
     if (hist) hist->clear();
     if (sweeps32_out) *sweeps32_out = 0;
@@ -570,7 +570,8 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
         DMRG_CHECK_CUDA(cudaMemcpyAsync(d_m32, m32.data(), sizeof(BJMat<float>) * nmat, cudaMemcpyHostToDevice, st));
         // stage 1: FP32 sweeps down to the FP32 rounding level
         const int s32 = bj_sweeps<float>(d_m32, d_off, nmat, njob, ne_max, ntile, (float*)Qall, d_norm,
-                                         kMaxSweeps32, kTol32, kStall32, kStallFrom32, kInner32, st, hist, &worst);
+                                         kMaxSweeps32, tol32 > 0.0 ? tol32 : kTol32, kStall32, kStallFrom32,
+                                         kInner32, st, hist, &worst);
         if (sweeps32_out) *sweeps32_out = s32;
         // stage 2 (FP64): V = V32 made orthonormal by two Newton-Schulz steps
         // V <- V (3 I - V^T V) / 2, then A = V^T rho V
