@@ -154,6 +154,10 @@ typedef struct {
     double decim_tol32;     /* decimation eigensolver: off(rho)/|rho| at which the FP32 stage of
                                large density-matrix blocks hands over to the FP64 sweeps (it also
                                stops at the FP32 rounding floor); 0 => 1e-5 */
+    int decim_fp64_units;   /* decimation eigensolver: 1 = the rotations of the FP64 sweeps that
+                               follow the FP32 stage run on the FP64 units; 0 (default) = in
+                               double-float arithmetic on the FP32 units (pairs of floats, ~48
+                               significant bits; GB300 runs FP32 ~64x faster than FP64) */
 } dmrg_options;
 
 typedef struct {

@@ -28,7 +28,8 @@ class Options(C.Structure):
                 ("verbose", C.c_int), ("tc_kchunk", C.c_int64), ("fp64_store", C.c_int), ("sigma_graph", C.c_int),
                 ("sigma_tune", C.c_int), ("sigma_tile_n", C.c_int), ("refine", C.c_int), ("max_refine", C.c_int),
                 ("fp64_tc", C.c_int), ("host_tier", C.c_int),
-                ("sigma_per_term", C.c_int), ("decim_tol32", C.c_double)]
+                ("sigma_per_term", C.c_int), ("decim_tol32", C.c_double),
+                ("decim_fp64_units", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -161,6 +161,7 @@ void dmrg_default_options(dmrg_options* o) {
     o->host_tier = 0;
     o->sigma_per_term = 0;
     o->decim_tol32 = 0.0;
+    o->decim_fp64_units = 0;
 }
 
 const char* dmrg_version(void) {

@@ -20,10 +20,13 @@ namespace dmrg {
 // Newton-Schulz steps) and A is transformed to that basis (V^T A V, FP64)
 // before the FP64 sweeps.  hist (optional) receives max over matrices of
 // off(A)/|A| before every sweep of both stages and at the end.  tol32 > 0
-// replaces the FP32 stage's target off(A)/|A| (default 1e-5).
+// replaces the FP32 stage's target off(A)/|A| (default 1e-5).  df_rot: the
+// rotations of the FP64 sweeps that follow an FP32 stage are applied in
+// double-float arithmetic (~48 significant bits on the FP32 units) instead of
+// FP64.
 int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double tol, cudaStream_t st,
                       const std::function<double*(int64_t)>& alloc_f,
                       const std::function<void(double*, int64_t)>& free_f, std::vector<double>* hist = nullptr,
-                      int* sweeps32 = nullptr, double tol32 = 0.0);
+                      int* sweeps32 = nullptr, double tol32 = 0.0, bool df_rot = true);
 
 }  // namespace dmrg

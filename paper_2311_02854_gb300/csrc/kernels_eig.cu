@@ -239,6 +239,130 @@ __global__ void __launch_bounds__(NT) bj_rows(const BJMat<T>* __restrict__ mats,
         }
 }
 
+// Double-float arithmetic for the FP64 sweeps of large matrices: GB300's FP32
+// units run ~64x its FP64 rate, and a pair (h, l) of floats with x = h + l
+// carries ~48 significant bits.  Products by Dekker's splitting through fma
+// (TwoProd), sums by Knuth's TwoSum; the _rn intrinsics keep the compiler
+// from contracting the error-free steps into fused operations.
+struct F2 {
+    float h, l;
+};
+__device__ __forceinline__ F2 f2_split(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double f2_join(F2 a) { return (double)a.h + (double)a.l; }
+// acc += a * b
+__device__ __forceinline__ void f2_fma(F2& acc, F2 a, F2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float s = __fadd_rn(acc.h, p);
+    const float v = __fsub_rn(s, acc.h);
+    const float t = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, v)), __fsub_rn(p, v));
+    const float lo = __fadd_rn(__fadd_rn(t, e), acc.l);
+    const float hi = __fadd_rn(s, lo);
+    acc.l = __fsub_rn(lo, __fsub_rn(hi, s));
+    acc.h = hi;
+}
+
+// bj_rows for FP64 matrices in double-float arithmetic (same tiling)
+__global__ void __launch_bounds__(NT) bj_rows_df(const BJMat<double>* __restrict__ mats,
+                                                 const int* __restrict__ job_off, int nmat, int round,
+                                                 const double* __restrict__ Qall, int ntile) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    F2* Qs = reinterpret_cast<F2*>(sm_raw);
+    F2* As = Qs + SB * LD;
+    const int job = blockIdx.x / ntile, tile = blockIdx.x % ntile;
+    const PairRef<double> pr = pair_of(mats, job_off, nmat, round, job);
+    if (!pr.live || tile * SB >= pr.M.n) return;
+    const double* Q = Qall + (int64_t)job * SB * SB;
+    const int n = pr.M.n, tid = threadIdx.x;
+    for (int e = tid; e < SB * SB; e += NT) {
+        const int a = e / SB, b = e % SB, col = tile * SB + b;
+        Qs[a * LD + b] = f2_split(Q[e]);
+        As[a * LD + b] = f2_split((col < n) ? pr.M.A[(int64_t)sub_index(pr, a) * n + col] : 0.0);
+    }
+    __syncthreads();
+    const int ty = tid / 16, tx = tid % 16;
+    F2 acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = {0.f, 0.f};
+#pragma unroll 2
+    for (int k = 0; k < SB; ++k) {
+        F2 qa[4], ab[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            qa[u] = Qs[k * LD + ty + 16 * u];
+            ab[u] = As[k * LD + tx + 16 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) f2_fma(acc[u][w], qa[u], ab[w]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int a = ty + 16 * u, col = tile * SB + tx + 16 * w;
+            if (col < n) pr.M.A[(int64_t)sub_index(pr, a) * n + col] = f2_join(acc[u][w]);
+        }
+}
+
+// bj_cols for FP64 matrices in double-float arithmetic (same tiling)
+__global__ void __launch_bounds__(NT) bj_cols_df(const BJMat<double>* __restrict__ mats,
+                                                 const int* __restrict__ job_off, int nmat, int round,
+                                                 const double* __restrict__ Qall, int ntile) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    F2* Qs = reinterpret_cast<F2*>(sm_raw);
+    F2* As = Qs + SB * LD;
+    const int job = blockIdx.x / ntile, tile = blockIdx.x % ntile;
+    const PairRef<double> pr = pair_of(mats, job_off, nmat, round, job);
+    if (!pr.live || tile * SB >= pr.M.n) return;
+    const double* Q = Qall + (int64_t)job * SB * SB;
+    const int n = pr.M.n, tid = threadIdx.x;
+    for (int e = tid; e < SB * SB; e += NT) Qs[(e / SB) * LD + e % SB] = f2_split(Q[e]);
+    for (int which = 0; which < 2; ++which) {
+        double* X = which ? pr.M.V : pr.M.A;
+        for (int e = tid; e < SB * SB; e += NT) {
+            const int a = e / SB, b = e % SB, row = tile * SB + a;
+            As[a * LD + b] = f2_split((row < n) ? X[(int64_t)row * n + sub_index(pr, b)] : 0.0);
+        }
+        __syncthreads();
+        const int ty = tid / 16, tx = tid % 16;
+        F2 acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < SB; ++k) {
+            F2 xa[4], qb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xa[u] = As[(ty + 16 * u) * LD + k];
+                qb[u] = Qs[k * LD + tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) f2_fma(acc[u][w], xa[u], qb[w]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int row = tile * SB + ty + 16 * u;
+                if (row < n) X[(int64_t)row * n + sub_index(pr, tx + 16 * w)] = f2_join(acc[u][w]);
+            }
+        __syncthreads();
+    }
+}
+
 // X[row tile, columns I u J] <- X[row tile, columns I u J] Q for X = A, then X = V
 template <typename T>
 __global__ void __launch_bounds__(NT) bj_cols(const BJMat<T>* __restrict__ mats, const int* __restrict__ job_off,
@@ -433,13 +557,19 @@ __global__ void __launch_bounds__(NT) bj_store(const BJMat<double>* __restrict__
 template <typename T>
 int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
               int ne_max, int ntile, T* Qall, double* d_norm, int max_sweeps, double tol, double stall,
-              double stall_from, int max_inner, cudaStream_t st, std::vector<double>* hist, double* final_worst) {
+              double stall_from, int max_inner, cudaStream_t st, std::vector<double>* hist, double* final_worst,
+              bool df = false) {
     const size_t smem = 2 * SB * LD * sizeof(T);
     static bool attr = false;
     if (!attr) {
         DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if constexpr (sizeof(T) == 8) {
+            static_assert(sizeof(F2) == sizeof(T), "double-float tiles take the shared memory of FP64 tiles");
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_rows_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_cols_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
         attr = true;
     }
     std::vector<double> nrm(2 * nmat);
@@ -462,8 +592,18 @@ int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
         prev = worst;
         for (int r = 0; r < ne_max - 1; ++r) {
             bj_solve<T><<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, max_inner);
-            bj_rows<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
-            bj_cols<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
+            bool done = false;
+            if constexpr (sizeof(T) == 8) {
+                if (df) {
+                    bj_rows_df<<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
+                    bj_cols_df<<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
+                    done = true;
+                }
+            }
+            if (!done) {
+                bj_rows<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
+                bj_cols<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
+            }
             launch_counter() += 3;
         }
         DMRG_CHECK_CUDA(cudaGetLastError());
@@ -491,7 +631,7 @@ __global__ void __launch_bounds__(NT) bj_sym(const BJMat<double>* __restrict__ m
 int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double tol, cudaStream_t st,
                       const std::function<double*(int64_t)>& alloc_f,
                       const std::function<void(double*, int64_t)>& free_f, std::vector<double>* hist,
-                      int* sweeps32_out, double tol32) {
+                      int* sweeps32_out, double tol32, bool df_rot) {
     const int nmat = (int)jobs.size();
     if (hist) hist->clear();
     if (sweeps32_out) *sweeps32_out = 0;
@@ -603,8 +743,11 @@ int block_jacobi_eigh(const std::vector<EigJob>& jobs, int max_sweeps, double to
         ++launch_counter();
     }
     // FP64 sweeps to the tolerance
+    // after an FP32 stage the rotations of the FP64 sweeps run in double-float
+    // arithmetic (~48 bits, the FP32 units' rate); small matrices stay FP64
     const int sweeps = bj_sweeps<double>(d_mats, d_off, nmat, njob, ne_max, ntile, Qall, d_norm, max_sweeps, tol,
-                                         kStall64, kStallFrom64, kInner64, st, hist, &worst);
+                                         kStall64, kStallFrom64, kInner64, st, hist, &worst,
+                                         two_stage && df_rot);
     bj_store<<<dim3(gx, nmat), NT, 0, st>>>(d_mats, d_jobs);
     ++launch_counter();
     DMRG_CHECK_CUDA(cudaGetLastError());

@@ -680,7 +680,7 @@ void decimate(Plan& P, const double* psi, int nr, int Dmax, bool forward, double
     std::vector<double> conv;
     P.stats.decim_sweeps_last = block_jacobi_eigh(
         jobs, 40, 1e-14, st, [&](int64_t n) { return P.alloc(n); }, [&](double* p, int64_t n) { P.free(p, n); },
-        &conv, &P.stats.decim_sweeps32_last, P.opt.decim_tol32);
+        &conv, &P.stats.decim_sweeps32_last, P.opt.decim_tol32, P.opt.decim_fp64_units == 0);
     for (int i = 0; i < 41; ++i) P.stats.decim_conv_last[i] = i < (int)conv.size() ? conv[i] : 0.0;
     P.stats.decim_nmat_last = (int)jobs.size();
     P.stats.decim_nmax_last = 0;
