@@ -125,10 +125,13 @@ struct DavOut {
 
 // One Davidson solve from the guesses in psi (nr x n; Ritz vectors on exit).
 // stall > 0: stop when the residual no longer falls near the mixed sigma's
-// noise floor: after at least 10 iterations, the best residual so far is below
-// stall * max|theta| and the best of the last 5 iterations is above 0.7 times
-// the best before them.  (Far above the floor, Davidson may stagnate for a
-// while and then converge, so a plateau alone is not a stall.)
+// noise floor: after at least kStallMin iterations, the best residual so far
+// is below stall * max|theta| and the best of the last kStallWin iterations is
+// above 0.7 times the best before them.  (Far above the floor, Davidson may
+// stagnate for a while and then converge, so a plateau alone is not a stall.)
+// From the next-bond guess of a converged wavefunction the K = 73 residual
+// reaches the floor in 4-5 iterations; a window of 3 stops 3 iterations later.
+constexpr int kStallMin = 6, kStallWin = 3;
 void davidson_run(Plan& P, double* psi, int nr, double tol, int max_iter, int precond, const DefectCorr* corr,
                   double stall, DavOut& out) {
     const int64_t n = P.dim;
@@ -340,9 +343,9 @@ void davidson_run(Plan& P, double* psi, int nr, double tol, int max_iter, int pr
             break;
         }
         if (it >= max_iter) break;
-        if (stall > 0.0 && it >= 10) {
-            const double before = *std::min_element(hist.begin(), hist.end() - 5);
-            const double recent = *std::min_element(hist.end() - 5, hist.end());
+        if (stall > 0.0 && it >= kStallMin) {
+            const double before = *std::min_element(hist.begin(), hist.end() - kStallWin);
+            const double recent = *std::min_element(hist.end() - kStallWin, hist.end());
             double tmax = 0.0;
             for (int i = 0; i < nr; ++i) tmax = std::max(tmax, std::fabs(theta[i]));
             if (std::min(before, recent) < stall * tmax && recent > 0.7 * before) {
