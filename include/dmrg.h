@@ -258,10 +258,13 @@ dmrg_status dmrg_plan(const double* h, const double* chol, int n_chol, double e_
  * left-orthonormal on 1..k-1 and right-orthonormal on k+2..K. */
 dmrg_status dmrg_set_bond(dmrg_plan_t plan, int k, void* stream);
 
-/* Canonical layout of the current bond.  dim = total length; n_sectors =
- * number of sector blocks.  If offsets != NULL it receives n_sectors+1
- * offsets; if qn != NULL it receives 6 ints per sector:
- * (N_L, 2Sz_L, c1, c2, d_l, d_r). */
+/* Canonical layout of the current bond (Sec. 2.1: the two-site wavefunction
+ * Psi(L, c1, c2, R) is block-sparse in the (N, 2Sz) quantum numbers; one dense
+ * d_l x d_r block, C order, per allowed (L, c1, c2, R), packed back to back).
+ * dim = total length; n_sectors = number of sector blocks.  If offsets !=
+ * NULL it receives n_sectors+1 offsets; if qn != NULL it receives 6 ints per
+ * sector: (N_L, 2Sz_L, c1, c2, d_l, d_r).  Returns DMRG_EINVAL without a
+ * current bond. */
 dmrg_status dmrg_layout(dmrg_plan_t plan, int64_t* dim, int* n_sectors, int64_t* offsets, int* qn);
 
 /* sigma = H psi (Eq. Sigma) for nvec vectors stored back to back (device,
@@ -360,9 +363,15 @@ dmrg_status dmrg_sweep(dmrg_plan_t plan, int n_sweeps, const int* D_schedule, do
  * are all equal. */
 dmrg_status dmrg_extrapolate(const double* w, const double* E, int n, double* e0, double* slope, double* rms);
 
-/* Write the current MPS (same format as the input file). */
+/* Write the current MPS (Sec. 2.1: the site tensors after the decimations
+ * so far, left-orthonormal left of the centre and right-orthonormal right of
+ * it) in the format of the input file.  DMRG_EIO if the file cannot be
+ * written. */
 dmrg_status dmrg_save_mps(dmrg_plan_t plan, const char* path);
 
+/* Copy the plan's counters (dmrg_stats_t above: phase times, algorithmic
+ * FLOPs of sigma (Tab. stat counts its GEMMs the same way), renormalisation
+ * and intermediates, bytes held, launches, solver histories) into *out. */
 dmrg_status dmrg_stats(dmrg_plan_t plan, dmrg_stats_t* out);
 
 /* One-line description of the last error of this plan (or of plan creation
