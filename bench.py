@@ -267,7 +267,9 @@ def run_mine(args):
              "decimation_device": (s_after["ms_decim"] - s_before["ms_decim"]) / 1e3 / args.steps,
              "renormalisation": (s_after["ms_renorm"] - s_before["ms_renorm"]) / 1e3 / args.steps,
              "host_planning": (s_after["ms_host_plan"] - s_before["ms_host_plan"]) / 1e3 / args.steps,
-             "autotuner": (s_after["ms_tune"] - s_before["ms_tune"]) / 1e3 / args.steps}
+             "autotuner": (s_after["ms_tune"] - s_before["ms_tune"]) / 1e3 / args.steps,
+             "intermediates_device": (s_after["ms_interm"] - s_before["ms_interm"]) / 1e3 / args.steps,
+             "hdiag_device": (s_after["ms_hdiag"] - s_before["ms_hdiag"]) / 1e3 / args.steps}
     # algorithmic FLOPs of the timed steps, from the library's counters: every
     # sigma call (each counted at its own bond's planned count), FP64-accurate
     # sigma calls, renormalisations and intermediates

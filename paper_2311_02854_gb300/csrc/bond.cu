@@ -1299,7 +1299,16 @@ void sigma_body(Plan& P, const double* psi, double* out, int nvec, cudaStream_t 
 void hdiag(Plan& P, double* out, cudaStream_t st) {
     DMRG_REQUIRE(P.bond > 0, DMRG_EINVAL, "no current bond (call dmrg_set_bond)");
     BufTable bt = bond_buffers(P, nullptr, out);
+    cudaEvent_t e0 = P.take_event(), e1 = P.take_event();
+    DMRG_CHECK_CUDA(cudaEventRecord(e0, st));
     P.hdiag_pl.run(bt, 1, st);
+    DMRG_CHECK_CUDA(cudaEventRecord(e1, st));
+    DMRG_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DMRG_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    P.stats.ms_hdiag += ms;
+    P.ev_pool.push_back(e0);
+    P.ev_pool.push_back(e1);
 }
 
 }  // namespace dmrg
