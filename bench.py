@@ -591,9 +591,10 @@ def run_sweep_probe(args):
     h, L, bonds, path = make_inputs(w, td, 1)
     plan = g.Plan(h, L, K, w["N"], w["twoS"], ds[-1], path, precision=PRECISIONS[args.precision],
                   tol=args.tol, max_iter=args.dav_iters, host_tier=int(args.host_tier),
+                  sigma_tune=int(args.sigma_tune), verbose=int(args.verbose),
                   fp64_store=int(args.fp64_store), fp64_tc=int(args.fp64_tc), refine=int(args.refine))
     keys = ("ms_davidson", "ms_decim", "ms_renorm", "ms_interm", "ms_sigma_dev", "ms_host_plan", "ms_hdiag",
-            "ms_tier_wait", "tier_out_bytes", "tier_in_bytes", "sigma_calls")
+            "ms_tier_wait", "tier_out_bytes", "tier_in_bytes", "sigma_calls", "ms_tune", "tunes")
     prev = plan.stats()
     for i, D in enumerate(ds):
         torch.cuda.synchronize()
@@ -678,6 +679,7 @@ def main():
                     help="D-ramped sweeps of the whole chain with the host tier; s/site per sweep")
     ap.add_argument("--sweep-d", default="500,1000,2000,3000", help="--sweep: bond dimension of each sweep")
     ap.add_argument("--host-tier", type=int, default=1, help="--sweep: environment blocks in pinned host memory")
+    ap.add_argument("--sigma-tune", type=int, default=1, help="--sweep: tile-shape autotuner on (1) or off (0)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -442,23 +442,49 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
     }
     starts.push_back(cs.size());
     const size_t nch = cs.empty() ? 0 : starts.size() - 1;
-    std::vector<std::pair<WorkList, WorkList>> built(nch);
-    std::vector<double> cfl(nch, 0.0);
+    // scratch offset of every contribution's phase-1 product inside its chunk
+    std::vector<int64_t> soff(cs.size() + 1, 0);
     std::vector<int64_t> cused(nch, 0);
-    // the chunks' work lists, built in parallel
-    parallel_for(nch, [&](size_t ch) {
-        WorkList& p1 = built[ch].first;
-        WorkList& p2 = built[ch].second;
-        std::vector<std::vector<Seg>> segs(outs.size());
-        std::vector<char> seen(outs.size(), 0);
-        std::vector<int> order;
+    for (size_t ch = 0; ch < nch; ++ch) {
         int64_t used = 0;
-        double fl = 0.0;
         for (size_t i = starts[ch]; i < starts[ch + 1]; ++i) {
+            soff[i] = used;
+            used += need_of(cs[i]);
+        }
+        cused[ch] = used;
+    }
+    // the chunks' items in units of at most kUnit on host threads: each unit's
+    // phase-1 blocks and, per output, its phase-2 segments; concatenated per
+    // chunk in item order (the result of lowering the items one by one)
+    constexpr size_t kUnit = 8192;
+    struct Unit {
+        size_t ch, a, b;
+        WorkList p1;
+        std::vector<std::pair<int, Seg>> osegs;
+        double fl = 0.0;
+    };
+    std::vector<Unit> units;
+    std::vector<size_t> unit_beg(nch + 1, 0);
+    for (size_t ch = 0; ch < nch; ++ch) {
+        unit_beg[ch] = units.size();
+        for (size_t a = starts[ch]; a < starts[ch + 1]; a += kUnit) {
+            Unit u;
+            u.ch = ch;
+            u.a = a;
+            u.b = std::min(starts[ch + 1], a + kUnit);
+            units.push_back(std::move(u));
+        }
+    }
+    unit_beg[nch] = units.size();
+    parallel_for(units.size(), [&](size_t ui) {
+        Unit& u = units[ui];
+        WorkList& p1 = u.p1;
+        double fl = 0.0;
+        for (size_t i = u.a; i < u.b; ++i) {
             const Contrib& c = cs[i];
             const int nreal = (!c.P.ident) + (!c.Q.ident) + (!c.R.ident);
             const bool unit = (c.alpha == 1.0 || c.alpha == -1.0);
-            const int64_t need = need_of(c);
+            const int64_t used = soff[i];
             bool pq_first = true;
             double cost = 0.0;
             int tc_ = 0;  // columns of the phase-1 product
@@ -471,11 +497,6 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
             } else if (!unit) {
                 tc_ = c.n;
             }
-            if (!seen[c.out]) {
-                seen[c.out] = 1;
-                order.push_back(c.out);
-            }
-            std::vector<Seg>& sv = segs[c.out];
             View T;
             T.buf = sbuf;
             T.off = used;
@@ -485,13 +506,12 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
                 if (pq_first) {
                     p1.add_block(used, sbuf, c.m, c.k2, T.ld, {make_seg(c.P, c.Q, c.k1, 1.0)}, TC_STORE_SPLIT, 0, 128,
                                  (float)c.alpha);
-                    sv.push_back(make_seg(T, c.R, c.k2, 1.0));
+                    u.osegs.push_back({c.out, make_seg(T, c.R, c.k2, 1.0)});
                 } else {
                     p1.add_block(used, sbuf, c.k1, c.n, T.ld, {make_seg(c.Q, c.R, c.k2, 1.0)}, TC_STORE_SPLIT, 0, 128,
                                  (float)c.alpha);
-                    sv.push_back(make_seg(c.P, T, c.k1, 1.0));
+                    u.osegs.push_back({c.out, make_seg(c.P, T, c.k1, 1.0)});
                 }
-                used += need;
                 continue;
             }
             // the two (or one) real factors X (m x k) and Y (k x n)
@@ -519,20 +539,48 @@ void ProductList::lower_tc(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int6
                 fl += 2.0 * c.m * c.n;
             }
             if (unit) {
-                sv.push_back(make_seg(X, Y, k, c.alpha));
+                u.osegs.push_back({c.out, make_seg(X, Y, k, c.alpha)});
             } else {
                 p1.add_block(used, sbuf, c.m, c.n, T.ld, {make_seg(X, Y, k, 1.0)}, TC_STORE_SPLIT, 0, 128,
                              (float)c.alpha);
-                sv.push_back(make_seg(T, I, c.n, 1.0));
-                used += need;
+                u.osegs.push_back({c.out, make_seg(T, I, c.n, 1.0)});
             }
+        }
+        u.fl = fl;
+    });
+    std::vector<std::pair<WorkList, WorkList>> built(nch);
+    std::vector<double> cfl(nch, 0.0);
+    parallel_for(nch, [&](size_t ch) {
+        WorkList& p1 = built[ch].first;
+        WorkList& p2 = built[ch].second;
+        std::vector<std::vector<Seg>> segs(outs.size());
+        std::vector<char> seen(outs.size(), 0);
+        std::vector<int> order;
+        for (size_t ui = unit_beg[ch]; ui < unit_beg[ch + 1]; ++ui) {
+            Unit& u = units[ui];
+            const int so = (int)p1.segs.size();
+            for (Tile t : u.p1.tiles) {
+                t.seg_beg += so;
+                t.seg_end += so;
+                p1.tiles.push_back(t);
+            }
+            p1.segs.insert(p1.segs.end(), u.p1.segs.begin(), u.p1.segs.end());
+            p1.flops += u.p1.flops;
+            for (const auto& os : u.osegs) {
+                if (!seen[os.first]) {
+                    seen[os.first] = 1;
+                    order.push_back(os.first);
+                }
+                segs[os.first].push_back(os.second);
+            }
+            cfl[ch] += u.fl;
+            u.p1 = WorkList();
+            std::vector<std::pair<int, Seg>>().swap(u.osegs);
         }
         for (int o : order) {
             const OutBlock& ob = outs[o];
             p2.add_block(ob.off, ob.buf, ob.m, ob.n, ob.ldc, segs[o], out_mode, kchunk, 128, 1.0f);
         }
-        cfl[ch] = fl;
-        cused[ch] = used;
     });
     for (size_t ch = 0; ch < nch; ++ch) {
         flops += cfl[ch];
@@ -696,29 +744,44 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         plans.push_back(std::move(cp));
         i = j;
     }
-    // pass 2 (chunks in parallel): the work lists of each chunk, with tensor
-    // maps keyed in a table of the chunk's own, merged into `maps` afterwards
+    // pass 2: the work lists.  Each chunk's items are cut into units of at
+    // most kUnit items that run on host threads, each with a tensor-map table
+    // of its own: a unit's phase-1 tiles and, per output block, its phase-2
+    // segments.  The units' tables are merged into `maps` in order, and each
+    // chunk's lists are concatenated from its units in order, so that the
+    // result is that of lowering the items one by one.
+    constexpr size_t kUnit = 8192;
     const size_t nch = plans.size();
-    std::vector<TmaWorkList> w1(nch), w2(nch);
-    std::vector<MapTable> local(nch);
-    std::vector<double> cfl(nch, 0.0);
-    auto build_chunk = [&](size_t ch) {
-        const ChunkPlan& cp = plans[ch];
-        MapTable& lm = local[ch];
-        TmaWorkList& p1 = w1[ch];
-        TmaWorkList& p2 = w2[ch];
+    struct Unit {
+        size_t ch, a, b;  // items [a, b) of chunk ch
+        MapTable lm;
+        TmaWorkList p1;
+        std::vector<std::pair<int, TSeg>> osegs;  // (output block, phase-2 segment), item order
         double fl = 0.0;
-        std::vector<std::vector<TSeg>> segs(outs.size());
-        std::vector<char> seen(outs.size(), 0);
-        std::vector<int> order;
-        for (size_t q = 0; q < cp.items.size(); ++q) {
+    };
+    std::vector<Unit> units;
+    std::vector<size_t> unit_beg(nch + 1, 0);
+    for (size_t ch = 0; ch < nch; ++ch) {
+        unit_beg[ch] = units.size();
+        const size_t ni = plans[ch].items.size();
+        for (size_t a = 0; a < std::max<size_t>(ni, 1); a += kUnit) {
+            Unit u;
+            u.ch = ch;
+            u.a = a;
+            u.b = std::min(ni, a + kUnit);
+            units.push_back(std::move(u));
+        }
+    }
+    unit_beg[nch] = units.size();
+    parallel_for(units.size(), [&](size_t ui) {
+        Unit& u = units[ui];
+        const ChunkPlan& cp = plans[u.ch];
+        MapTable& lm = u.lm;
+        TmaWorkList& p1 = u.p1;
+        double fl = 0.0;
+        for (size_t q = u.a; q < u.b; ++q) {
             const Contrib& c = cs[cp.i + q];
             const Item& it = cp.items[q];
-            if (!seen[c.out]) {
-                seen[c.out] = 1;
-                order.push_back(c.out);
-            }
-            std::vector<TSeg>& sv = segs[c.out];
             View T;
             if (it.kind >= 2) {
                 const auto& g = cp.groups[it.grp];
@@ -734,22 +797,80 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
                     fl += 2.0 * c.m * c.k1 * c.k2 + 2.0 * c.m * c.k2 * c.n;
                     p1.add_block(T.off, sbuf, c.m, c.k2, T.ld, {make_tseg(lm, c.P, c.Q, c.m, c.k2, c.k1, 1.0, vstride, nv)},
                                  TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                    sv.push_back(make_tseg(lm, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv));
+                    u.osegs.push_back({c.out, make_tseg(lm, T, c.R, c.m, c.n, c.k2, 1.0, vstride, nv)});
                 } else {
                     fl += 2.0 * c.k1 * c.k2 * c.n + 2.0 * c.m * c.k1 * c.n;
                     p1.add_block(T.off, sbuf, c.k1, c.n, T.ld, {make_tseg(lm, c.Q, c.R, c.k1, c.n, c.k2, 1.0, vstride, nv)},
                                  TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                    sv.push_back(make_tseg(lm, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv));
+                    u.osegs.push_back({c.out, make_tseg(lm, c.P, T, c.m, c.n, c.k1, 1.0, vstride, nv)});
                 }
             } else if (it.kind == 2) {
                 fl += it.fl;
                 p1.add_block(T.off, sbuf, c.m, c.n, T.ld, {make_tseg(lm, it.X, it.Y, c.m, c.n, it.k, 1.0, vstride, nv)},
                              TC_STORE_SPLIT, 0, (float)c.alpha, tile_n);
-                sv.push_back(make_tseg(lm, T, I, c.m, c.n, c.n, 1.0, vstride, nv));
+                u.osegs.push_back({c.out, make_tseg(lm, T, I, c.m, c.n, c.n, 1.0, vstride, nv)});
             } else {
                 fl += it.fl;
-                sv.push_back(make_tseg(lm, it.X, it.Y, c.m, c.n, it.k, c.alpha, vstride, nv));
+                u.osegs.push_back({c.out, make_tseg(lm, it.X, it.Y, c.m, c.n, it.k, c.alpha, vstride, nv)});
             }
+        }
+        u.fl = fl;
+    });
+    // merge the units' map tables in order (sequential: first-seen order of the keys)
+    std::vector<std::vector<int>> gi(units.size());
+    for (size_t ui = 0; ui < units.size(); ++ui) {
+        gi[ui].resize(units[ui].lm.keys.size());
+        for (size_t x = 0; x < gi[ui].size(); ++x) gi[ui][x] = maps.get(units[ui].lm.keys[x]);
+    }
+    parallel_for(units.size(), [&](size_t ui) {
+        Unit& u = units[ui];
+        for (TSeg& sg : u.p1.segs) {
+            sg.a_map = gi[ui][sg.a_map];
+            sg.b_map = gi[ui][sg.b_map];
+        }
+        for (auto& os : u.osegs) {
+            os.second.a_map = gi[ui][os.second.a_map];
+            os.second.b_map = gi[ui][os.second.b_map];
+        }
+        u.lm.clear();
+    });
+    // per chunk (in parallel): phase 1 = the units' tiles in order; phase 2 =
+    // one block per output with its segments in item order, outputs in the
+    // order of their first item
+    std::vector<TmaWorkList> w1(nch), w2(nch);
+    std::vector<double> cfl(nch, 0.0);
+    parallel_for(nch, [&](size_t ch) {
+        TmaWorkList& p1 = w1[ch];
+        TmaWorkList& p2 = w2[ch];
+        size_t nt = 0, ns = 0;
+        for (size_t ui = unit_beg[ch]; ui < unit_beg[ch + 1]; ++ui) {
+            nt += units[ui].p1.tiles.size();
+            ns += units[ui].p1.segs.size();
+        }
+        p1.tiles.reserve(nt);
+        p1.segs.reserve(ns);
+        std::vector<std::vector<TSeg>> segs(outs.size());
+        std::vector<char> seen(outs.size(), 0);
+        std::vector<int> order;
+        for (size_t ui = unit_beg[ch]; ui < unit_beg[ch + 1]; ++ui) {
+            Unit& u = units[ui];
+            const int so = (int)p1.segs.size();
+            for (Tile t : u.p1.tiles) {
+                t.seg_beg += so;
+                t.seg_end += so;
+                p1.tiles.push_back(t);
+            }
+            p1.segs.insert(p1.segs.end(), u.p1.segs.begin(), u.p1.segs.end());
+            for (const auto& os : u.osegs) {
+                if (!seen[os.first]) {
+                    seen[os.first] = 1;
+                    order.push_back(os.first);
+                }
+                segs[os.first].push_back(os.second);
+            }
+            cfl[ch] += u.fl;
+            u.p1 = TmaWorkList();
+            std::vector<std::pair<int, TSeg>>().swap(u.osegs);
         }
         for (int o : order) {
             const OutBlock& ob = outs[o];
@@ -757,18 +878,8 @@ void ProductList::lower_tma(int8_t sbuf_, int8_t ibuf, int ild, int64_t cap, int
         }
         p1.order_tiles();
         p2.order_tiles();
-        cfl[ch] = fl;
-    };
-    parallel_for(nch, build_chunk);
-    // merge the chunks' map tables (in chunk order) and renumber their segments
+    });
     for (size_t ch = 0; ch < nch; ++ch) {
-        std::vector<int> gi(local[ch].keys.size());
-        for (size_t x = 0; x < gi.size(); ++x) gi[x] = maps.get(local[ch].keys[x]);
-        for (TmaWorkList* w : {&w1[ch], &w2[ch]})
-            for (TSeg& sg : w->segs) {
-                sg.a_map = gi[sg.a_map];
-                sg.b_map = gi[sg.b_map];
-            }
         flops += cfl[ch];
         scratch_elems = std::max(scratch_elems, plans[ch].used);
         tchunks.emplace_back(std::move(w1[ch]), std::move(w2[ch]));
