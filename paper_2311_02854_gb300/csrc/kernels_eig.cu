@@ -267,98 +267,6 @@ __device__ __forceinline__ void f2_fma(F2& acc, F2 a, F2 b) {
     acc.h = hi;
 }
 
-// bj_solve for FP64 matrices with the subproblem and its Q held and rotated in
-// double-float arithmetic; the rotation angles are computed in FP64 from the
-// joined entries (same skip rules as bj_solve<double>)
-__global__ void __launch_bounds__(NT) bj_solve_df(const BJMat<double>* __restrict__ mats,
-                                                  const int* __restrict__ job_off, int nmat, int round,
-                                                  double* __restrict__ Qall, int max_inner) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    F2* S = reinterpret_cast<F2*>(sm_raw);  // SB x LD
-    F2* Qs = S + SB * LD;                    // SB x LD
-    __shared__ F2 cs[BB], msn[BB];           // c and -s of each rotation of a round
-    __shared__ int pp[BB], qq[BB];
-    __shared__ int rot_on[BB];
-    __shared__ int rotated;
-    const PairRef<double> pr = pair_of(mats, job_off, nmat, round, blockIdx.x);
-    double* Q = Qall + (int64_t)blockIdx.x * SB * SB;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < SB * SB; e += NT) {
-        const int a = e / SB, b = e % SB;
-        S[a * LD + b] = f2_split(pr.live ? pr.M.A[(int64_t)sub_index(pr, a) * pr.M.n + sub_index(pr, b)] : 0.0);
-        Qs[a * LD + b] = {a == b ? 1.f : 0.f, 0.f};
-    }
-    __syncthreads();
-    for (int sw = 0; pr.live && sw < max_inner; ++sw) {
-        if (tid == 0) rotated = 0;
-        __syncthreads();
-        for (int r = 0; r < SB - 1; ++r) {
-            if (tid < BB) {
-                int p, q;
-                rr_pair(r, tid, SB, p, q);
-                double c = 1.0, sn = 0.0;
-                const double apq = f2_join(S[p * LD + q]), app = f2_join(S[p * LD + p]), aqq = f2_join(S[q * LD + q]);
-                if (fabs(apq) > pr.M.floor && fabs(apq) > RelSkip<double>::v * sqrt(fabs(app * aqq)) &&
-                    (fabs(app) >= pr.M.tau || fabs(aqq) >= pr.M.tau)) {
-                    const double tau = (aqq - app) / (2.0 * apq);
-                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    sn = t * c;
-                    if (sn != 0.0) rotated = 1;
-                }
-                cs[tid] = f2_split(c);
-                msn[tid] = f2_split(-sn);
-                rot_on[tid] = sn != 0.0;
-                pp[tid] = p;
-                qq[tid] = q;
-            }
-            __syncthreads();
-            for (int e = tid; e < BB * SB; e += NT) {  // rows p, q of S
-                const int u = e / SB, k = e % SB;
-                if (!rot_on[u]) continue;
-                const int p = pp[u], q = qq[u];
-                const F2 c = cs[u], ms = msn[u], x = S[p * LD + k], y = S[q * LD + k];
-                F2 xn{0.f, 0.f}, yn{0.f, 0.f};
-                f2_fma(xn, c, x);
-                f2_fma(xn, ms, y);  // c x - s y
-                f2_fma(yn, c, y);
-                f2_fma(yn, {-ms.h, -ms.l}, x);  // s x + c y
-                S[p * LD + k] = xn;
-                S[q * LD + k] = yn;
-            }
-            __syncthreads();
-            for (int e = tid; e < BB * SB; e += NT) {  // columns p, q of S and Q
-                const int u = e / SB, k = e % SB;
-                if (!rot_on[u]) continue;
-                const int p = pp[u], q = qq[u];
-                const F2 c = cs[u], ms = msn[u], s_ = {-ms.h, -ms.l};
-                F2 x = S[k * LD + p], y = S[k * LD + q], xn{0.f, 0.f}, yn{0.f, 0.f};
-                f2_fma(xn, c, x);
-                f2_fma(xn, ms, y);
-                f2_fma(yn, s_, x);
-                f2_fma(yn, c, y);
-                S[k * LD + p] = xn;
-                S[k * LD + q] = yn;
-                x = Qs[k * LD + p];
-                y = Qs[k * LD + q];
-                xn = {0.f, 0.f};
-                yn = {0.f, 0.f};
-                f2_fma(xn, c, x);
-                f2_fma(xn, ms, y);
-                f2_fma(yn, s_, x);
-                f2_fma(yn, c, y);
-                Qs[k * LD + p] = xn;
-                Qs[k * LD + q] = yn;
-            }
-            __syncthreads();
-        }
-        const int any = rotated;  // read by every thread before the next reset
-        __syncthreads();
-        if (!any) break;
-    }
-    for (int e = tid; e < SB * SB; e += NT) Q[e] = f2_join(Qs[(e / SB) * LD + e % SB]);
-}
-
 // bj_rows for FP64 matrices in double-float arithmetic (same tiling)
 __global__ void __launch_bounds__(NT) bj_rows_df(const BJMat<double>* __restrict__ mats,
                                                  const int* __restrict__ job_off, int nmat, int round,
@@ -659,7 +567,6 @@ int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
         DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if constexpr (sizeof(T) == 8) {
             static_assert(sizeof(F2) == sizeof(T), "double-float tiles take the shared memory of FP64 tiles");
-            DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_solve_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_rows_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             DMRG_CHECK_CUDA(cudaFuncSetAttribute(bj_cols_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
@@ -684,17 +591,16 @@ int bj_sweeps(const BJMat<T>* d_mats, const int* d_off, int nmat, int njob,
         if (prev >= 0.0 && worst < stall_from * stall_from && worst > stall * stall * prev) break;
         prev = worst;
         for (int r = 0; r < ne_max - 1; ++r) {
+            bj_solve<T><<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, max_inner);
             bool done = false;
             if constexpr (sizeof(T) == 8) {
                 if (df) {
-                    bj_solve_df<<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, max_inner);
                     bj_rows_df<<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
                     bj_cols_df<<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
                     done = true;
                 }
             }
             if (!done) {
-                bj_solve<T><<<njob, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, max_inner);
                 bj_rows<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
                 bj_cols<T><<<njob * ntile, NT, smem, st>>>(d_mats, d_off, nmat, r, Qall, ntile);
             }
