@@ -350,11 +350,21 @@ int64_t scratch_cap_f64(const Plan& P) {
 // Intermediates: Int[rows x nnz] = W[rows x nops] * Family[nops x nnz]
 // ---------------------------------------------------------------------------
 
-void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops) {
-    int64_t total = 0, wtot = 0;
+void interm_bases(Interms& im, const Block* blocks[2]) {
+    int64_t total = 0;
     for (auto& IF : im.fams) {
         const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
         IF.base = total;
+        total += (int64_t)IF.rows.size() * f.stride;
+    }
+}
+
+void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops, bool bases_set) {
+    if (!bases_set) interm_bases(im, blocks);
+    // (im is read-only from here: a host thread may be lowering lists that refer to it)
+    int64_t total = 0, wtot = 0;
+    for (const auto& IF : im.fams) {
+        const Family& f = blocks[IF.owner]->lay.fams[IF.src_fam];
         total += (int64_t)IF.rows.size() * f.stride;
         wtot += (int64_t)IF.rows.size() * round_up(f.nops(), 8);
     }
@@ -799,31 +809,17 @@ void set_bond(Plan& P, int k) {
     const Block& R = *P.right[k + 1];
     build_layout(P, k);
     build_sigma_terms(P.I, L.lay, R.lay, k, P.sp);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, P.stream);
     const Block* blocks[2] = {&L, &R};
-    double fl = 0.0;
-    form_interms(P, P.sp.interms, blocks, P.interm, fl);
-    cudaEventRecord(e1, P.stream);
-    DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    P.stats.ms_interm += ms;
-    P.stats.interm_flops = fl;
-    P.stats.interm_flops_total += fl;
-    const int esz = (P.mixed() ? 2 * (1 + P.lo_pieces()) : 0) + (P.f64_store() ? 8 : 0);
-    P.stats.interm_bytes = P.interm.n * esz;
-    P.stats.store_bytes = (L.n + R.n) * esz;
+    interm_bases(P.sp.interms, blocks);  // offsets the sigma lists refer to
+    int maxd = std::max({L.lay.basis.dmax(), R.lay.basis.dmax(), 1});
+    ensure_ident(P, maxd);
+    P.sigma_fp64_ready = false;
+    P.sigma_units_pl.clear();
+    P.sigma_units_ready = false;
 
     // sigma contributions (FP64 views; the bf16 copy of psi is padded)
-    const auto hs0 = std::chrono::steady_clock::now();
     ProductList& pl = P.sigma_pl;
-    pl.clear();
-    for (const Plan::Sector& s : P.layout) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
+    ProductList& tl = P.sigma_tc;
     const LocalOps& Y = P.sp.y;
     // the blocks of a term's operators depend only on the ket sector of their
     // side; terms are taken in blocks on host threads and their contributions
@@ -832,96 +828,22 @@ void set_bond(Plan& P, int k) {
     const size_t nterm = P.sp.terms.size();
     const size_t tblk = std::max<size_t>(1, (nterm + 63) / 64);
     const size_t nblk = (nterm + tblk - 1) / tblk;
-    std::vector<std::vector<Contrib>> part(nblk);
-    parallel_for(nblk, [&](size_t b) {
-        std::vector<OpLookup> lcache(nbl), rcache(nbr);
-        std::vector<Contrib>& out = part[b];
-        for (size_t ti = b * tblk; ti < std::min(nterm, (b + 1) * tblk); ++ti) {
-            const Term3& t = P.sp.terms[ti];
-            const LocalOp& M = Y.ops[t.y];
-            const int pR = ref_parity(R.lay, P.sp.interms, t.R);
-            for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
-            for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
-            for (size_t si = 0; si < P.layout.size(); ++si) {
-                const Plan::Sector& s = P.layout[si];
-                const OpLookup& ol = lcache[s.il];
-                if (!ol.ok) continue;
-                const OpLookup& orr = rcache[s.ir];
-                if (!orr.ok) continue;
-                const int nl = L.lay.basis.qn[s.il].n;
-                const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
-                for (int y2 = 0; y2 < 16; ++y2) {
-                    const double mv = M.at(y2, s.y);
-                    if (mv == 0.0) continue;
-                    const int os = P.sector_idx[16 * ol.j + y2];
-                    if (os < 0) continue;
-                    const Plan::Sector& o = P.layout[os];
-                    DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
-                    const int e = M.parity * nl + pR * (nl + ny);
-                    const double zeta = (e & 1) ? -1.0 : 1.0;
-                    Contrib c;
-                    c.out = os;
-                    c.P = ol.v;  // O^L_eff : d_jl x d_il
-                    c.Q.buf = BUF_PSI;
-                    c.Q.off = s.off;
-                    c.Q.ld = s.dr;  // Psi_s : d_il x d_ir
-                    c.R = orr.v.T();  // (O^R_eff)^T : d_ir x d_jr
-                    c.m = o.dl;
-                    c.k1 = s.dl;
-                    c.k2 = s.dr;
-                    c.n = o.dr;
-                    c.alpha = t.c * zeta * mv;
-                    c.qsec = (int)si;
-                    c.term = (int)ti;
-                    out.push_back(c);
-                }
-            }
-        }
-    });
-    size_t ntot = 0;
-    for (auto& v : part) ntot += v.size();
-    pl.cs.reserve(ntot);
-    for (auto& v : part) pl.cs.insert(pl.cs.end(), v.begin(), v.end());
-    const int64_t nitems = (int64_t)ntot;
-    int maxd = std::max({L.lay.basis.dmax(), R.lay.basis.dmax(), 1});
-    ensure_ident(P, maxd);
-    P.sigma_fp64_ready = false;
-    P.sigma_units_pl.clear();
-    P.sigma_units_ready = false;
-    if (P.mixed()) {
-        ProductList& tl = P.sigma_tc;
-        tl.clear();
-        tl.outs = pl.outs;
-        // the tensor-core list reads psi from its padded bf16 copy
-        tl.cs.resize(pl.cs.size());
-        const size_t cb = 1 << 16;
-        parallel_for((pl.cs.size() + cb - 1) / cb, [&](size_t b) {
-            for (size_t x = b * cb; x < std::min(pl.cs.size(), (b + 1) * cb); ++x) {
-                Contrib c = pl.cs[x];
-                const Plan::Sector& s = P.layout[c.qsec];
-                c.Q.off = s.poff;
-                c.Q.ld = (int)round_up(s.dr, 8);
-                tl.cs[x] = c;
-            }
-        });
-        // vectors per launch (block Davidson passes up to n_roots at once)
-        const int G = std::max(1, P.opt.n_roots);
-        int64_t vs[kMaxBufs] = {};
-        vs[BUF_PSI] = P.dim_pad;
-        const int64_t cap = std::max<int64_t>(scratch_cap(P) / G, 1 << 20);
-        SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
-        const double t_terms = host_ms_since(hs0);
-        if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
-        // lists of over a million products keep the default shape: it won every
-        // measurement at that size (K = 54 and K = 73 middle bonds), and the
-        // timing of the candidates costs 0.3-1 s per new bond there
-        else if (P.opt.sigma_tune && P.opt.tc_kchunk <= 0 && !P.opt.sigma_per_term &&
-                 tl.cs.size() <= ((size_t)1 << 20))
-            shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
-        const double t_tune = host_ms_since(hs0);
+    // vectors per launch (block Davidson passes up to n_roots at once)
+    const int G = std::max(1, P.opt.n_roots);
+    int64_t vs[kMaxBufs] = {};
+    vs[BUF_PSI] = P.dim_pad;
+    const int64_t cap = std::max<int64_t>(scratch_cap(P) / G, 1 << 20);
+    SigmaShape shape{128, P.opt.tc_kchunk > 0 ? P.opt.tc_kchunk : (P.nsplit == 3 ? kChunkSigmaX6 : kChunkSigmaTC)};
+    if (P.opt.sigma_tile_n > 0) shape.tn = P.opt.sigma_tile_n;
+    int64_t nitems = 0;
+    bool tune_later = false;
+    double t_terms = 0.0, t_lower = 0.0, t_count = 0.0, plan_ms = 0.0;
+    auto lower_and_count = [&]() {
+        const auto c0 = std::chrono::steady_clock::now();
         tl.chunk_per_term = P.opt.sigma_per_term != 0;
         tl.lower_tma(BUF_SCR, BUF_ID, P.id_n, cap, shape.kchunk, TC_ATOMIC_F64, vs, G, shape.tn);
-        const double t_lower = host_ms_since(hs0);
+        t_lower += host_ms_since(c0);
+        const auto c1 = std::chrono::steady_clock::now();
         P.stats.sigma_tile_n = shape.tn;
         P.stats.sigma_kchunk = shape.kchunk;
         tl.cs.clear();
@@ -965,7 +887,141 @@ void set_bond(Plan& P, int k) {
             P.stats.sigma_load_bytes[ph][0] += cnt[x].load[0];
             P.stats.sigma_load_bytes[ph][1] += cnt[x].load[1];
         }
-        const double t_count = host_ms_since(hs0);
+        t_count = host_ms_since(c1);
+    };
+    // The host part of the sigma plan (contributions, their lowering into
+    // tiles and tensor maps, counts) reads host structures only and runs on a
+    // thread while the GPU forms the intermediates; the tuner, allocations and
+    // uploads follow on this thread.
+    auto host_plan = [&]() {
+        const auto h0 = std::chrono::steady_clock::now();
+        pl.clear();
+        for (const Plan::Sector& s : P.layout) pl.outs.push_back({BUF_OUT, s.off, s.dl, s.dr, s.dr});
+        std::vector<std::vector<Contrib>> part(nblk);
+        parallel_for(nblk, [&](size_t b) {
+            std::vector<OpLookup> lcache(nbl), rcache(nbr);
+            std::vector<Contrib>& out = part[b];
+            for (size_t ti = b * tblk; ti < std::min(nterm, (b + 1) * tblk); ++ti) {
+                const Term3& t = P.sp.terms[ti];
+                const LocalOp& M = Y.ops[t.y];
+                const int pR = ref_parity(R.lay, P.sp.interms, t.R);
+                for (int i = 0; i < nbl; ++i) lcache[i] = lookup(L.lay, P.sp.interms, t.L, i, BUF_L);
+                for (int i = 0; i < nbr; ++i) rcache[i] = lookup(R.lay, P.sp.interms, t.R, i, BUF_R);
+                for (size_t si = 0; si < P.layout.size(); ++si) {
+                    const Plan::Sector& s = P.layout[si];
+                    const OpLookup& ol = lcache[s.il];
+                    if (!ol.ok) continue;
+                    const OpLookup& orr = rcache[s.ir];
+                    if (!orr.ok) continue;
+                    const int nl = L.lay.basis.qn[s.il].n;
+                    const int ny = kSiteQN[s.y / 4].n + kSiteQN[s.y % 4].n;
+                    for (int y2 = 0; y2 < 16; ++y2) {
+                        const double mv = M.at(y2, s.y);
+                        if (mv == 0.0) continue;
+                        const int os = P.sector_idx[16 * ol.j + y2];
+                        if (os < 0) continue;
+                        const Plan::Sector& o = P.layout[os];
+                        DMRG_REQUIRE(o.ir == orr.j, DMRG_EINVAL, "sigma term breaks the symmetry");
+                        const int e = M.parity * nl + pR * (nl + ny);
+                        const double zeta = (e & 1) ? -1.0 : 1.0;
+                        Contrib c;
+                        c.out = os;
+                        c.P = ol.v;  // O^L_eff : d_jl x d_il
+                        c.Q.buf = BUF_PSI;
+                        c.Q.off = s.off;
+                        c.Q.ld = s.dr;  // Psi_s : d_il x d_ir
+                        c.R = orr.v.T();  // (O^R_eff)^T : d_ir x d_jr
+                        c.m = o.dl;
+                        c.k1 = s.dl;
+                        c.k2 = s.dr;
+                        c.n = o.dr;
+                        c.alpha = t.c * zeta * mv;
+                        c.qsec = (int)si;
+                        c.term = (int)ti;
+                        out.push_back(c);
+                    }
+                }
+            }
+        });
+        size_t ntot = 0;
+        for (auto& v : part) ntot += v.size();
+        pl.cs.reserve(ntot);
+        for (auto& v : part) pl.cs.insert(pl.cs.end(), v.begin(), v.end());
+        nitems = (int64_t)ntot;
+        if (P.mixed()) {
+            tl.clear();
+            tl.outs = pl.outs;
+            // the tensor-core list reads psi from its padded bf16 copy
+            tl.cs.resize(pl.cs.size());
+            const size_t cb = 1 << 16;
+            parallel_for((pl.cs.size() + cb - 1) / cb, [&](size_t b) {
+                for (size_t x = b * cb; x < std::min(pl.cs.size(), (b + 1) * cb); ++x) {
+                    Contrib c = pl.cs[x];
+                    const Plan::Sector& s = P.layout[c.qsec];
+                    c.Q.off = s.poff;
+                    c.Q.ld = (int)round_up(s.dr, 8);
+                    tl.cs[x] = c;
+                }
+            });
+            t_terms = host_ms_since(h0);
+            // lists of over a million products keep the default shape: it won every
+            // measurement at that size (K = 54 and K = 73 middle bonds), and the
+            // timing of the candidates costs 0.3-1 s per new bond there
+            tune_later = P.opt.sigma_tile_n <= 0 && P.opt.sigma_tune && P.opt.tc_kchunk <= 0 &&
+                         !P.opt.sigma_per_term && tl.cs.size() <= ((size_t)1 << 20);
+            if (!tune_later) lower_and_count();
+        } else {
+            t_terms = host_ms_since(h0);
+            P.f64_tiles(pl);
+            pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), kChunkF64);
+        }
+        plan_ms = host_ms_since(h0);
+    };
+    std::exception_ptr plan_err;
+    std::thread planner([&]() {
+        try {
+            host_plan();
+        } catch (...) {
+            plan_err = std::current_exception();
+        }
+    });
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, P.stream);
+    double fl = 0.0;
+    try {
+        form_interms(P, P.sp.interms, blocks, P.interm, fl, true);
+        cudaEventRecord(e1, P.stream);
+        DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));
+    } catch (...) {
+        planner.join();
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    planner.join();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (plan_err) std::rethrow_exception(plan_err);
+    P.stats.ms_interm += ms;
+    P.stats.interm_flops = fl;
+    P.stats.interm_flops_total += fl;
+    const int esz = (P.mixed() ? 2 * (1 + P.lo_pieces()) : 0) + (P.f64_store() ? 8 : 0);
+    P.stats.interm_bytes = P.interm.n * esz;
+    P.stats.store_bytes = (L.n + R.n) * esz;
+    const auto hs0 = std::chrono::steady_clock::now();
+    if (P.mixed()) {
+        double t_tune = 0.0;
+        if (tune_later) {
+            const auto c0 = std::chrono::steady_clock::now();
+            shape = tune_sigma_shape(P, k, tl, cap, shape.kchunk, vs, G);
+            t_tune = host_ms_since(c0);
+            lower_and_count();
+        }
+        const auto u0 = std::chrono::steady_clock::now();
         ensure_scratch(P, (int64_t)G * tl.scratch_elems);
         ensure_psi_pieces(P, (int64_t)G * P.dim_pad);
         for (auto& ch : tl.tchunks) {
@@ -976,8 +1032,7 @@ void set_bond(Plan& P, int k) {
         if (P.opt.verbose)
             fprintf(stderr, "[dmrg] bond %d sigma planning: terms %.0f ms, tuning %.0f ms, lowering %.0f ms, "
                             "counts %.0f ms, upload %.0f ms (%zu chunks)\n",
-                    k, t_terms, t_tune - t_terms, t_lower - t_tune, t_count - t_lower, host_ms_since(hs0) - t_count,
-                    tl.tchunks.size());
+                    k, t_terms, t_tune, t_lower, t_count, host_ms_since(u0), tl.tchunks.size());
         P.stats.sigma_maps = (int64_t)tl.maps.keys.size();
         P.stats.sigma_flops = tl.flops;
         // padded bf16 copy of psi: one split job per sector
@@ -991,8 +1046,6 @@ void set_bond(Plan& P, int k) {
             DMRG_CHECK_CUDA(cudaMemcpyAsync(P.d_psi_jobs, jobs.data(), jobs.size() * sizeof(SplitJob),
                                             cudaMemcpyHostToDevice, P.stream));
     } else {
-        P.f64_tiles(pl);
-        pl.lower(BUF_SCR, BUF_ID, P.ident_n, scratch_cap(P), kChunkF64);
         ensure_scratch(P, std::max<int64_t>(pl.scratch_elems, 1));
         pl.upload(P.stream);
         P.sigma_fp64_ready = true;
@@ -1091,7 +1144,7 @@ void set_bond(Plan& P, int k) {
         DMRG_CHECK_CUDA(
             cudaMemcpyAsync(m.d_sec_q, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, P.stream));
     }
-    P.stats.ms_host_plan += host_ms_since(hs0);
+    P.stats.ms_host_plan += plan_ms + host_ms_since(hs0);
     P.drop_graphs();  // captured for the previous bond's work lists
     P.bond = k;
     DMRG_CHECK_CUDA(cudaStreamSynchronize(P.stream));

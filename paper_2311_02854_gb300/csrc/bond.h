@@ -5,7 +5,11 @@
 
 namespace dmrg {
 
-void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops);
+// offsets of the intermediates in their store (what the sigma lists refer to)
+void interm_bases(Interms& im, const Block* blocks[2]);
+// bases_set: interm_bases already ran for im (im is then only read)
+void form_interms(Plan& P, Interms& im, const Block* blocks[2], IntermStore& S, double& flops,
+                  bool bases_set = false);
 void free_interms(Plan& P, IntermStore& S);
 void free_block(Plan& P, std::unique_ptr<Block>& b);
 void ensure_ident(Plan& P, int n);
