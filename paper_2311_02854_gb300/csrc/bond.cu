@@ -978,8 +978,11 @@ void set_bond(Plan& P, int k) {
         plan_ms = host_ms_since(h0);
     };
     std::exception_ptr plan_err;
+    int device = 0;  // the thread frees the old lists' device arrays on the plan's device
+    DMRG_CHECK_CUDA(cudaGetDevice(&device));
     std::thread planner([&]() {
         try {
+            DMRG_CHECK_CUDA(cudaSetDevice(device));
             host_plan();
         } catch (...) {
             plan_err = std::current_exception();
