@@ -1,0 +1,93 @@
+"""Checks at the benchmark's sizes, where the CPU oracle cannot run: properties
+that hold at any size, on the seeded workloads of the benchmark (Gaussian
+sector split, middle bond).
+
+* K=36, D=1000 (N=36, 144 Cholesky vectors): the FP64-unit sigma is
+  symmetric, <y|H x> = <H y|x> to rounding; the FP64-accurate tensor-core
+  sigma equals it to 1e-12 relative; the BF16X3 sigma to the mixed bound.
+* K=73, D=3000 (N=114, 292 Cholesky vectors), the bench's launch
+  configuration (BF16X3, one vector, CUDA graph, default tiles): the mixed
+  sigma is symmetric to its own error, and two calls on the same vector agree
+  to the rounding of the FP64 drains."""
+import os
+
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from tests.helpers import cuda_torch, gpu_lib
+
+pytestmark = pytest.mark.gpu
+
+K36 = dict(K=36, N=36, twoS=0, D=1000, n_chol=144, ell=3.0, h_min=-4.0, w=1.45)
+K73 = dict(K=73, N=114, twoS=0, D=3000, n_chol=292, ell=8.0, h_min=-6.0, w=1.45)
+
+
+def _case(tmp_path, c):
+    K = c["K"]
+    k = K // 2
+    h, L = si.make_integrals(K, c["n_chol"], ell=c["ell"], h_min=c["h_min"], seed=0)
+    bonds = si.bond_sectors(K, c["N"], c["twoS"], c["D"], split="gaussian", width_n=c["w"], width_s=c["w"])
+    mps = si.random_mps(K, c["N"], c["twoS"], bonds, center=k, seed=2)
+    path = os.path.join(str(tmp_path), f"mps_{K}.bin")
+    si.write_mps(path, mps)
+    return h, L, path, k
+
+
+def _sig(plan, torch, v):
+    x = torch.from_numpy(v.copy()).cuda()
+    y = torch.empty_like(x)
+    plan.sigma(x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def test_k36_d1000_sigma_symmetry_and_engines(tmp_path):
+    torch = cuda_torch()
+    g = gpu_lib()
+    c = K36
+    h, L, path, k = _case(tmp_path, c)
+    out = {}
+    for name, prec in (("fp64", 0), ("fp64tc", 4), ("bf16x3", 1)):
+        plan = g.Plan(h, L, c["K"], c["N"], c["twoS"], c["D"], path, precision=prec)
+        plan.set_bond(k)
+        dim = plan.dim
+        x = si.random_vector(dim, seed=1)
+        y = si.random_vector(dim, seed=3)
+        out[name] = (x, y, _sig(plan, torch, x), _sig(plan, torch, y))
+        plan.close()
+    x, y, hx, hy = out["fp64"]
+    scale = np.linalg.norm(hx) * np.linalg.norm(y)
+    asym = abs(y @ hx - hy @ x) / scale
+    e_tc = np.linalg.norm(out["fp64tc"][2] - hx) / np.linalg.norm(hx)
+    e_mx = np.linalg.norm(out["bf16x3"][2] - hx) / np.linalg.norm(hx)
+    print(f"K=36 D=1000 dim {len(x)}: FP64 asymmetry {asym:.1e}, FP64_TC vs FP64 {e_tc:.1e}, "
+          f"BF16X3 vs FP64 {e_mx:.1e}")
+    assert asym < 1e-13
+    assert e_tc < 1e-12
+    assert e_mx < 2e-5
+
+
+def test_k73_d3000_mixed_sigma_in_the_bench_configuration(tmp_path):
+    torch = cuda_torch()
+    g = gpu_lib()
+    c = K73
+    h, L, path, k = _case(tmp_path, c)
+    plan = g.Plan(h, L, c["K"], c["N"], c["twoS"], c["D"], path, precision=1)
+    plan.set_bond(k)
+    dim = plan.dim
+    x = si.random_vector(dim, seed=1)
+    y = si.random_vector(dim, seed=3)
+    hx = _sig(plan, torch, x)
+    hy = _sig(plan, torch, y)
+    hx2 = _sig(plan, torch, x)
+    st = plan.stats()
+    plan.close()
+    asym = abs(y @ hx - hy @ x) / (np.linalg.norm(hx) * np.linalg.norm(y))
+    rep = np.linalg.norm(hx2 - hx) / np.linalg.norm(hx)
+    print(f"K=73 D=3000 dim {dim}: mixed asymmetry {asym:.1e}, repeat {rep:.1e}, "
+          f"{st['sigma_chunks']} chunks, tile {st['sigma_tile_n']}")
+    assert dim > 5_000_000 and st["sigma_chunks"] >= 3
+    assert asym < 2e-5
+    assert rep < 1e-12
+    assert np.isfinite(hx).all() and np.linalg.norm(hx) > 0
